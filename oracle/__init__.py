@@ -1,0 +1,17 @@
+"""FP64 CPU oracle for the Legendre-multipole 3PCF (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+leg of ``bench.py`` may import this package.  It shares no code with the CUDA
+library in ``paper_2604_08855_gb300``; the two meet only through the seeded
+input generators.
+
+Parity status of each function (what pins it is listed in the tests):
+  ylm    pinned: scipy's complex spherical harmonics, the addition theorem,
+         orthonormality by quadrature.
+  alm    pinned through zeta (hand geometries, triplets) and the addition
+         theorem on its own output.
+  zeta   pinned: O(N^3) triplet sum with numpy Legendre polynomials, the
+         l = 0 closed form with scipy's cKDTree neighbour counts, hand-built
+         geometries with printed P_l values, invariances.
+"""
+from .oracle import build, ylm, alm, zeta, max_threads, lib_path  # noqa: F401

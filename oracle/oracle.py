@@ -1,0 +1,141 @@
+"""ctypes wrapper around ``ctb_oracle.c`` (FP64 brute force; test infrastructure).
+
+The shared object is compiled with the host gcc into ``oracle/_build`` on first
+use (or by ``__graft_entry__.build()``).  No function here touches a GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ctb_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libctb_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, IEEE arithmetic)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            os.makedirs(_BUILD, exist_ok=True)
+            tmp = _LIB + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                   "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+        vp = ctypes.c_void_p
+        lib.oracle_ylm.argtypes = [i32, d, d, d, vp]
+        lib.oracle_ylm.restype = None
+        lib.oracle_alm.argtypes = [vp, vp, i64, d, d, d, i32, i32, vp, i64, vp, vp, i32]
+        lib.oracle_alm.restype = i32
+        lib.oracle_zeta.argtypes = [vp, vp, i64, d, d, d, i32, i32, vp, i64,
+                                    vp, vp, vp, vp, vp, vp, d, i32]
+        lib.oracle_zeta.restype = i32
+        lib.oracle_max_threads.argtypes = []
+        lib.oracle_max_threads.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _points(xyz, w):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    if xyz.ndim != 2 or xyz.shape[1] != 3:
+        raise ValueError("xyz must be (n, 3)")
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (xyz.shape[0],):
+            raise ValueError("w must be (n,)")
+    return xyz, w
+
+
+def _prim(prim):
+    if prim is None:
+        return None
+    return np.ascontiguousarray(prim, dtype=np.int64)
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def ylm(lmax: int, dirs) -> np.ndarray:
+    """Real orthonormal Y_lm, index l*l + l + m, at each unit direction."""
+    lib = _load()
+    dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+    nc = (lmax + 1) ** 2
+    out = np.zeros((dirs.shape[0], nc))
+    row = np.zeros(nc)
+    for i, (x, y, z) in enumerate(dirs):
+        lib.oracle_ylm(lmax, float(x), float(y), float(z), _ptr(row))
+        out[i] = row
+    return out
+
+
+def alm(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, nthreads=0):
+    """a_lm(p, b) for the given primaries: array [np][nbins][(lmax+1)^2]."""
+    lib = _load()
+    xyz, w = _points(xyz, w)
+    prim = _prim(prim)
+    n = xyz.shape[0]
+    np_ = n if prim is None else prim.shape[0]
+    nc = (lmax + 1) ** 2
+    out = np.zeros((np_, nbins, nc))
+    npairs = ctypes.c_int64(0)
+    rc = lib.oracle_alm(_ptr(xyz), _ptr(w), n, float(box), float(rmin), float(rmax),
+                        int(nbins), int(lmax), _ptr(prim), np_, _ptr(out),
+                        ctypes.byref(npairs), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_alm rejected its arguments (rc={rc})")
+    return out
+
+
+def zeta(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, amb_tol=0.0, nthreads=0):
+    """zeta_l(b1, b2) and its diagnostics, summed over the given primaries.
+
+    Returns a dict with ``zeta`` and ``gram`` ([lmax+1][nbins][nbins]),
+    ``wpairs`` and ``selfw`` ([nbins]), ``npairs`` and ``namb`` (ints).
+    """
+    lib = _load()
+    xyz, w = _points(xyz, w)
+    prim = _prim(prim)
+    n = xyz.shape[0]
+    np_ = n if prim is None else prim.shape[0]
+    shape = (lmax + 1, nbins, nbins)
+    z = np.zeros(shape)
+    g = np.zeros(shape)
+    wp = np.zeros(nbins)
+    sw = np.zeros(nbins)
+    npairs = ctypes.c_int64(0)
+    namb = ctypes.c_int64(0)
+    rc = lib.oracle_zeta(_ptr(xyz), _ptr(w), n, float(box), float(rmin), float(rmax),
+                         int(nbins), int(lmax), _ptr(prim), np_, _ptr(z), _ptr(g),
+                         _ptr(wp), _ptr(sw), ctypes.byref(npairs), ctypes.byref(namb),
+                         float(amb_tol), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_zeta rejected its arguments (rc={rc})")
+    return {"zeta": z, "gram": g, "wpairs": wp, "selfw": sw,
+            "npairs": int(npairs.value), "namb": int(namb.value)}
