@@ -1,0 +1,353 @@
+"""Benchmark: Legendre-multipole 3PCF on one GB300 (prints one JSON line).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp32|bf16x3|tf32] [--workload thomas_1m]
+
+A step is one full pass of the hot path over the workload: ingest + cell sort
+(ctb_set_points from device-resident float64 inputs), pair multipoles,
+contraction and the FP64 reduction (ctb_compute).  Default workload: 1,000,000
+Thomas-process points in a periodic cube L = 1000 (10,000 parents, sigma = 5,
+weights U[0.5, 1.5], seed 1), r in [5, 200] with 20 linear bins, l_max = 10.
+
+value  pair-multipole updates/s = binned ordered pairs x (l_max+1)^2 / step time
+e2e    the same through the C ABI with HOST float64 inputs and a HOST zeta
+       (host->device copies and the result read-back inside the timed region)
+
+--impl reference times the FP64 CPU oracle (the slow, obviously correct
+restatement of the method) on a bounded sample of primaries of the same
+workload, on the host cores.  Under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair-multipole updates/s (zeta_ell 3PCF, 1 GB300)"
+UNIT = "updates/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload(name: str):
+    from paper_2604_08855_gb300 import synth
+    if name == "thomas_1m":
+        xyz, w = synth.thomas_1m()
+        return xyz, w, synth.config_params(2), {
+            "workload": "thomas_1m", "n_points": 1_000_000, "box": 1000.0, "r_min": 5.0, "r_max": 200.0,
+            "nbins": 20, "ell_max": 10, "periodic": True, "clustering": "Thomas, 10k parents, sigma 5",
+            "weights": "U[0.5,1.5]"}
+    if name == "uniform_20k":
+        xyz, w = synth.uniform_20k()
+        return xyz, w, synth.config_params(1), {
+            "workload": "uniform_20k", "n_points": 20_000, "box": 1000.0, "r_min": 10.0, "r_max": 100.0,
+            "nbins": 10, "ell_max": 10, "periodic": True, "weights": "unit"}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def flops_per_pair(lmax: int) -> int:
+    """Algorithmic FP32 FLOPs of one pair in the pair kernel's harmonic loop
+    (FMA = 2): separation norm and direction, the complex power w (x+iy)^m,
+    the monic Legendre recurrence and one FMA per accumulated coefficient."""
+    L = lmax
+    f = 5 + 3  # r^2 (2 FMA + 1 MUL) and the direction (3 MUL)
+    f += 1 + (2 if L >= 1 else 0) + 5 * max(0, L - 1)  # m = 0 column
+    if L >= 1:
+        f += 2 + 6 * (L - 1)  # w (x+iy)^m, m = 1..L
+        for m in range(1, L + 1):
+            f += 2 + (4 if m + 1 <= L else 0) + 7 * max(0, L - m - 1)
+    return f
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+
+
+def oracle_rate(xyz, w, kw, target_s: float, seed: int = 7):
+    """Time the oracle on a growing sample of primaries until ~target_s of CPU work."""
+    import oracle
+    from paper_2604_08855_gb300 import synth
+    oracle.build()
+    nc = (kw["lmax"] + 1) ** 2
+    k = 32
+    while True:
+        prim = synth.sample_primaries(xyz.shape[0], k, seed=seed)
+        t0 = time.perf_counter()
+        res = oracle.zeta(xyz, w, prim=prim, **kw)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * target_s or k >= xyz.shape[0]:
+            break
+        k = min(xyz.shape[0], int(k * max(2.0, min(16.0, 0.5 * target_s / max(dt, 1e-3)))))
+    return res["npairs"] * nc / dt, k, dt, res["npairs"]
+
+
+def run_reference(args):
+    world, rank, _ = dist_init(args)
+    if rank != 0:
+        return
+    xyz, w, kw, cfg = workload(args.workload)
+    import oracle
+    oracle.build()
+    from paper_2604_08855_gb300 import synth
+    nc = (kw["lmax"] + 1) ** 2
+    cores = oracle.max_threads()
+    # size the per-step sample to about 2 s of CPU work
+    rate, _, _, _ = oracle_rate(xyz, w, kw, target_s=2.0)
+    per_pair = max(1.0, 33510.0 if args.workload == "thomas_1m" else 84.0)
+    k = int(max(8, min(xyz.shape[0], 2.0 * rate / nc / per_pair)))
+    times, pairs = [], []
+    for step in range(args.warmup + args.steps):
+        prim = synth.sample_primaries(xyz.shape[0], k, seed=1000 + step)
+        t0 = time.perf_counter()
+        res = oracle.zeta(xyz, w, prim=prim, **kw)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            pairs.append(res["npairs"])
+    total_t = sum(times)
+    value = sum(pairs) * nc / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{k} seeded primaries per step x all {xyz.shape[0]} secondaries"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def run_ours(args):
+    world, rank, local = dist_init(args)
+    import torch
+    from paper_2604_08855_gb300 import build as ctb_build
+    if rank == 0 or world == 1:
+        ctb_build.build()
+    barrier(world)
+    from paper_2604_08855_gb300 import ctb
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    xyz, w, kw, cfg = workload(args.workload)
+    nc = (kw["lmax"] + 1) ** 2
+    est = ctb.CTB(**kw)
+    stream = torch.cuda.current_stream(dev)
+    est.set_stream(stream)
+    if args.precision != "fp32":
+        est.set_option(ctb.OPT_PRECISION, {"bf16x3": ctb.PREC_BF16X3, "tf32": ctb.PREC_TF32}[args.precision])
+    d_xyz = torch.from_numpy(xyz).to(dev)
+    d_w = torch.from_numpy(w).to(dev)
+    d_zeta = torch.zeros(est.zeta_shape, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        est.set_points(d_xyz, d_w)
+        est.compute(out=d_zeta)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pair_ms, launches, npairs = [], 0, 0
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            pair_ms.append(est.timings()[2])
+            launches += est.launch_count()
+            npairs = est.pair_count()
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - wall0
+    barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = max_over_ranks(world, sum(step_ms) / 1e3)
+    updates = npairs * nc
+    value = world * args.steps * updates / t_total
+    ms_per_step = 1e3 * t_total / args.steps
+
+    # end to end through the public API with host buffers
+    zh = np.zeros(est.zeta_shape)
+    e2e_t = []
+    for k in range(max(2, min(args.steps, 5)) + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        est.set_points(xyz, w)
+        est.compute(out=zh)
+        dt = time.perf_counter() - t0
+        if k > 0:
+            e2e_t.append(dt)
+    e2e_s = max_over_ranks(world, float(np.mean(e2e_t)))
+    e2e = {"value": world * updates / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(xyz.nbytes + w.nbytes), "d2h_bytes_per_step": int(zh.nbytes + 8)}
+
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    pair_s = float(np.mean(pair_ms)) / 1e3
+    achieved = npairs * flops_per_pair(kw["lmax"]) / pair_s / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**cfg, "precision": args.precision, "l2": "flushed (256 MB write) before every step",
+                   "inputs": "device-resident float64 xyz, w"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_pair", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_note": f"FP32 FMA pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                  f"{sm_max:.0f} MHz ({pk_kind} max clock)",
+                     "flops_per_pair": flops_per_pair(kw["lmax"]), "pair_kernel_ms": 1e3 * pair_s},
+        "pairs_per_step": npairs,
+        "ms_per_zeta_ell": ms_per_step / (kw["lmax"] + 1),
+        "wall_s": wall,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, k, dt, _ = oracle_rate(xyz, w, kw, target_s=args.cpu_seconds)
+        import oracle
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                                "sample": f"{k} seeded primaries x all {xyz.shape[0]} secondaries, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    est.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32"])
+    ap.add_argument("--workload", default="thomas_1m")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

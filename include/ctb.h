@@ -1,0 +1,200 @@
+/*
+ * ctb.h -- C ABI of libctb: Legendre-multipole three-point correlation
+ * function (3PCF) on one GB300 GPU.
+ *
+ * The method (cTreeBalls paper, "Implementation" section): every catalogue
+ * point in turn is the pivot (here "primary") of the triangles it closes; all
+ * its neighbours inside the search range are found, and the multipole bins
+ * are filled with the harmonic coefficients of the neighbours' directions
+ * ("Statement of need": the 3PCF mapped onto an orthogonal basis whose
+ * coefficients cost pair-count time, after Szapudi 2004 and Slepian &
+ * Eisenstein).  The paper writes no formula; this library computes
+ *
+ *   a_lm(p,b)      = sum_{j != p, r_pj in bin b} w_j Y_lm(rhat_pj)
+ *   zeta_l(b1,b2)  = 4 pi/(2l+1) * sum_p w_p sum_{m=-l..l} a_lm(p,b1) a_lm(p,b2)
+ *
+ * with real orthonormal Y_lm, linear half-open bins
+ * [r_min + b D, r_min + (b+1) D), D = (r_max - r_min)/nbins, minimum-image
+ * separations in a periodic cube of side `box` (box > 0) or plain separations
+ * in open space (box <= 0).  j = k terms are included; pairs at zero
+ * separation are never binned.  By the addition theorem
+ *   zeta_l(b1,b2) = sum_p w_p sum_{j,k} w_j w_k P_l(rhat_pj . rhat_pk)
+ *                   [b_j = b1][b_k = b2].
+ *
+ * Conventions for every entry point:
+ *  - All functions return CTB_OK (0) or a negative CTB_ERR_* code, except
+ *    ctb_create (NULL on failure), ctb_destroy and ctb_last_error.  No
+ *    exception, abort or device trap crosses this boundary.  After a failure
+ *    ctb_last_error() describes it.
+ *  - Pointers marked "host or device" may point to host memory or to device
+ *    memory of the current CUDA device; the library tells them apart with
+ *    cudaPointerGetAttributes.  Inputs are copied; the caller keeps its
+ *    buffers and may reuse them as soon as the call returns.
+ *  - Work is issued on the context's stream (ctb_set_stream; default: the
+ *    legacy default stream); calls that return results to the host
+ *    synchronise that stream before returning.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef CTB_H
+#define CTB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctb_ctx ctb_ctx;
+
+/* status codes */
+#define CTB_OK 0
+#define CTB_ERR_ARG (-1)        /* invalid argument (see each call)              */
+#define CTB_ERR_NONFINITE (-2)  /* a coordinate or weight is NaN or infinite      */
+#define CTB_ERR_OOM (-3)        /* device allocation failed                       */
+#define CTB_ERR_CUDA (-4)       /* a CUDA call or kernel launch failed            */
+#define CTB_ERR_TIMEOUT (-5)    /* a bounded device-side wait gave up             */
+#define CTB_ERR_STATE (-6)      /* call out of order (e.g. compute before points) */
+#define CTB_ERR_UNSUPPORTED (-7)/* option value not available in this build       */
+
+/* largest ell_max a context accepts */
+#define CTB_LMAX_CAP 20
+/* largest number of radial bins a context accepts */
+#define CTB_NBINS_CAP 64
+
+/* option keys for ctb_set_option */
+#define CTB_OPT_PRECISION 1      /* contraction precision, CTB_PREC_* (default FP32)        */
+#define CTB_OPT_CELLS_PER_RMAX 2 /* grid cells per r_max along an axis, 1..64 (0 = auto)    */
+#define CTB_OPT_BIN_CAPACITY 3   /* per-warp neighbour-list capacity per bin, 256..65536    */
+#define CTB_OPT_WARPS_PER_BLOCK 4/* pair-kernel warps per block, 1..16 (0 = auto)           */
+#define CTB_OPT_CHUNK_PRIMARIES 5/* primaries per pair-kernel launch, >= 1024 (0 = auto)    */
+#define CTB_OPT_DETERMINISTIC 6  /* 1: fixed reduction order (default 1)                    */
+
+/* contraction precisions (zeta = M^T W M per ell on the tensor cores or not) */
+#define CTB_PREC_FP32 0   /* plain FP32 on the CUDA cores                       */
+#define CTB_PREC_BF16X3 1 /* tcgen05 kind::f16, hi/lo BF16 split, 3 products     */
+#define CTB_PREC_TF32 2   /* tcgen05 kind::tf32, one product                     */
+
+/*
+ * Create a context for one estimator configuration.
+ *   box      side of the periodic cube; box <= 0 selects open (non-periodic)
+ *            space
+ *   r_min    inner edge of bin 0, >= 0
+ *   r_max    outer edge of the last bin, > r_min; periodic: r_max <= box/2
+ *   nbins    number of linear radial bins, 1..CTB_NBINS_CAP
+ *   ell_max  largest multipole, 0..CTB_LMAX_CAP
+ * Returns a new context, or NULL if an argument is invalid or no CUDA device
+ * is usable (ctb_last_error(NULL) then says why).  The context binds to the
+ * CUDA device current at this call.
+ */
+ctb_ctx* ctb_create(double box, double r_min, double r_max, int nbins, int ell_max);
+
+/*
+ * Load a catalogue (paper, "Implementation": the points that act as pivots
+ * and as neighbours).  Ingests, builds the uniform cell grid and sorts the
+ * points into cell order on the device.
+ *   xyz  [n][3] float64, row-major, host or device.  Periodic: any finite
+ *        value, wrapped into [0, box).
+ *   w    [n] float64 weights (may be negative), host or device; NULL means
+ *        unit weights.
+ *   n    number of points, 0 <= n < 2^31.
+ * Errors: CTB_ERR_ARG (n out of range, xyz NULL with n > 0),
+ * CTB_ERR_NONFINITE (any coordinate or weight not finite; the context then
+ * holds no points), CTB_ERR_OOM, CTB_ERR_CUDA.
+ */
+int ctb_set_points(ctb_ctx* ctx, const double* xyz, const double* w, int64_t n);
+
+/*
+ * Compute zeta_l(b1,b2) over all points as primaries.
+ *   zeta_out  [(ell_max+1)][nbins][nbins] float64, host or device, written
+ *             in full (the matrix is symmetric in b1, b2).
+ * Errors: CTB_ERR_STATE (no ctb_set_points yet), CTB_ERR_ARG (zeta_out
+ * NULL), CTB_ERR_OOM, CTB_ERR_CUDA, CTB_ERR_TIMEOUT.
+ */
+int ctb_compute(ctb_ctx* ctx, double* zeta_out);
+
+/*
+ * As ctb_compute, with the primaries restricted to the listed points (all
+ * points stay secondaries).  Summing the results of a partition of the
+ * primaries reproduces ctb_compute up to rounding.
+ *   primary_idx  [m] int64 indices into the catalogue of ctb_set_points,
+ *                host or device, each in [0, n); duplicates count twice.
+ *   m            number of primaries, >= 0.
+ * Errors: as ctb_compute, plus CTB_ERR_ARG for an index out of range.
+ */
+int ctb_compute_subset(ctb_ctx* ctx, const int64_t* primary_idx, int64_t m, double* zeta_out);
+
+/*
+ * Export a_lm(p, b) of the listed primaries (debug / parity; the same
+ * coefficients the contraction consumes, rounded to float32).
+ *   primary_idx  [m] int64 catalogue indices, host or device
+ *   alm_out      [m][nbins][(ell_max+1)^2] float32, host or device;
+ *                coefficient (l, m) of the real basis at index l*l + l + m,
+ *                Y_l,+m ~ cos(m phi), Y_l,-m ~ sin(m phi), Condon-Shortley
+ *                phase included.
+ */
+int ctb_get_alm(ctb_ctx* ctx, const int64_t* primary_idx, int64_t m, float* alm_out);
+
+/*
+ * Compute zeta for k independent catalogues in one pass (mock batches for
+ * covariance estimates).  All catalogues share the context's box, bins and
+ * ell_max; catalogue i has n[i] points at xyz[i] (host or device, [n_i][3])
+ * and weights w[i] (NULL pointer or NULL array: unit weights).
+ *   zeta_out  [k][(ell_max+1)][nbins][nbins] float64, host or device.
+ * The context's own catalogue (ctb_set_points) is left unchanged.
+ * Errors: CTB_ERR_ARG (k < 1, a NULL xyz[i] with n[i] > 0, n[i] out of
+ * range), CTB_ERR_NONFINITE, CTB_ERR_OOM, CTB_ERR_CUDA, CTB_ERR_TIMEOUT.
+ */
+int ctb_compute_batch(ctb_ctx* ctx, const double* const* xyz, const double* const* w,
+                      const int64_t* n, int k, double* zeta_out);
+
+/* Set an option (CTB_OPT_*).  Returns CTB_ERR_ARG for an unknown key or a value
+ * out of range, CTB_ERR_UNSUPPORTED for a precision this build cannot run. */
+int ctb_set_option(ctb_ctx* ctx, int key, int64_t value);
+
+/* Issue all further work on `stream` (a cudaStream_t of the context's device,
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL = legacy default. */
+int ctb_set_stream(ctb_ctx* ctx, void* stream);
+
+/*
+ * Route the library's device allocations through a caller's allocator (e.g.
+ * the PyTorch caching allocator).  alloc(bytes, user) returns device memory
+ * or NULL; free(ptr, user) releases it.  Pass alloc = NULL to go back to
+ * cudaMallocAsync on the context's stream.  Buffers already held are
+ * released first, so call this before ctb_set_points.
+ */
+int ctb_set_allocator(ctb_ctx* ctx, void* (*alloc)(size_t bytes, void* user),
+                      void (*free_fn)(void* ptr, void* user), void* user);
+
+/*
+ * Per-stage device times of the last ctb_set_points / ctb_compute* call, in
+ * milliseconds, measured with CUDA events on the context's stream:
+ *   [0] ingest  [1] sort + grid  [2] pair multipoles  [3] pack
+ *   [4] contraction  [5] reduce + normalise
+ * Writes min(cap, 6) values; returns the number written.
+ */
+int ctb_get_timings(ctb_ctx* ctx, double* ms_per_stage, int cap);
+
+/* Number of CUDA kernels the library launched during the last ctb_set_points
+ * plus the last ctb_compute (observability: what one full pass costs in
+ * launches). */
+int ctb_get_launch_count(ctb_ctx* ctx, uint64_t* kernels);
+
+/* Number of ordered (primary, secondary) pairs binned by the last compute. */
+int ctb_get_pair_count(ctb_ctx* ctx, uint64_t* pairs);
+
+/* Release the context and all device memory it holds.  NULL is a no-op. */
+void ctb_destroy(ctb_ctx* ctx);
+
+/* Text of the last error on ctx (or of the last failed ctb_create on this
+ * thread when ctx is NULL).  Valid until the next call on the same context. */
+const char* ctb_last_error(const ctb_ctx* ctx);
+
+/* Library version string. */
+const char* ctb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTB_H */

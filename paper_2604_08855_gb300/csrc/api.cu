@@ -1,0 +1,683 @@
+// api.cu -- the libctb C ABI (include/ctb.h): context, buffers, orchestration.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctb_internal.cuh"
+
+using namespace ctb;
+
+namespace ctb {
+thread_local unsigned long long g_launches = 0;
+}
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+thread_local std::string g_create_err;
+
+constexpr int kStages = 6;
+constexpr int kMaxChunkEvents = 256;
+
+}  // namespace
+
+struct ctb_ctx {
+  int dev = 0;
+  int nsm = 0;
+  double box = 0, rmin = 0, rmax = 0;
+  int nbins = 0, lmax = 0;
+  int periodic = 0;
+  // options
+  int precision = CTB_PREC_FP32;
+  int cells_per_rmax = 0;
+  uint32_t cap = 1024;
+  int wpb = 0;
+  int64_t chunk = 0;
+  int deterministic = 1;
+  cudaStream_t st = nullptr;
+  void* (*alloc_fn)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* user = nullptr;
+  std::string err;
+  // catalogue
+  int64_t n = -1;
+  Geom g{};
+  double unit = 0;
+  double origin[3] = {0, 0, 0};
+  Layout lay{};
+  int Lk = 0;
+  float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];
+  bool tables_ready = false;
+  // device buffers
+  Buf xyz_stage, w_stage, key0, val0, key1, val1, hist, scan_tmp, pts_in, pts, s2i, i2s, cell_start;
+  Buf flags, bbox_part, lists, M, wprim, partial, zeta, prim, counters, norm, slot, idx64, alm;
+  cudaEvent_t ev[2 + 3 * kMaxChunkEvents + 4] = {};
+  bool ev_ready = false;
+  double t_ms[kStages] = {0, 0, 0, 0, 0, 0};
+  uint64_t npairs = 0;
+  unsigned long long launches_points = 0, launches_compute = 0;
+};
+
+namespace {
+
+int fail(ctb_ctx* c, int code, const std::string& what) {
+  c->err = what;
+  return code;
+}
+
+int cuda_fail(ctb_ctx* c, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? CTB_ERR_OOM : CTB_ERR_CUDA, msg);
+}
+
+#define CK(ctx, call)                                                 \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);        \
+  } while (0)
+
+void release(ctb_ctx* c, Buf& b) {
+  if (!b.p) return;
+  if (c->free_fn)
+    c->free_fn(b.p, c->user);
+  else
+    cudaFreeAsync(b.p, c->st);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// grow-only device buffer
+cudaError_t ensure(ctb_ctx* c, Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  release(c, b);
+  size_t want = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->alloc_fn) {
+    p = c->alloc_fn(want, c->user);
+    if (!p) return cudaErrorMemoryAllocation;
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, want, c->st);
+    if (e != cudaSuccess) return e;
+  }
+  b.p = p;
+  b.bytes = want;
+  return cudaSuccess;
+}
+
+template <class T>
+T* P(Buf& b) {
+  return static_cast<T*>(b.p);
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void release_all(ctb_ctx* c) {
+  Buf* all[] = {&c->xyz_stage, &c->w_stage, &c->key0, &c->val0, &c->key1, &c->val1, &c->hist,
+                &c->scan_tmp, &c->pts_in, &c->pts, &c->s2i, &c->i2s, &c->cell_start, &c->flags,
+                &c->bbox_part, &c->lists, &c->M, &c->wprim, &c->partial, &c->zeta, &c->prim,
+                &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm};
+  for (Buf* b : all) release(c, *b);
+  c->tables_ready = false;
+}
+
+int ensure_events(ctb_ctx* c) {
+  if (c->ev_ready) return CTB_OK;
+  for (auto& e : c->ev) CK(c, cudaEventCreate(&e));
+  c->ev_ready = true;
+  return CTB_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
+}
+
+// normalisation per slot and the slot table of the context's layout
+int ensure_tables(ctb_ctx* c) {
+  if (c->tables_ready) return CTB_OK;
+  c->Lk = lmax_kernel(c->lmax);
+  make_layout(c->Lk, &c->lay);
+  fill_beta(c->beta);
+  std::vector<float> norm(c->lay.row, 0.f);
+  for (int l = 0; l <= c->Lk; ++l)
+    for (int m = -l; m <= l; ++m) norm[c->lay.slot[l * l + l + m]] = (float)norm_lm(l, m);
+  CK(c, ensure(c, c->norm, norm.size() * sizeof(float)));
+  CK(c, ensure(c, c->slot, sizeof(c->lay.slot)));
+  CK(c, cudaMemcpyAsync(c->norm.p, norm.data(), norm.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->slot.p, c->lay.slot, sizeof(c->lay.slot), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaStreamSynchronize(c->st));  // host sources go out of scope
+  c->tables_ready = true;
+  return CTB_OK;
+}
+
+int bits_for(uint32_t ncells) {
+  int b = 0;
+  while (b < 32 && (1ull << b) < (unsigned long long)ncells) ++b;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// catalogue load: ingest -> radix sort by cell -> gather -> cell table
+
+int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
+  if (n < 0 || n >= (int64_t)1 << 31) return fail(c, CTB_ERR_ARG, "n out of range [0, 2^31)");
+  if (n > 0 && !xyz) return fail(c, CTB_ERR_ARG, "xyz is NULL");
+  CK(c, cudaSetDevice(c->dev));
+  int r = ensure_events(c);
+  if (r) return r;
+  c->n = -1;
+  const double* dxyz = xyz;
+  const double* dw = w;
+  if (n > 0 && !is_device_ptr(xyz)) {
+    CK(c, ensure(c, c->xyz_stage, (size_t)n * 3 * sizeof(double)));
+    CK(c, cudaMemcpyAsync(c->xyz_stage.p, xyz, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    dxyz = P<double>(c->xyz_stage);
+  }
+  if (n > 0 && w && !is_device_ptr(w)) {
+    CK(c, ensure(c, c->w_stage, (size_t)n * sizeof(double)));
+    CK(c, cudaMemcpyAsync(c->w_stage.p, w, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    dw = P<double>(c->w_stage);
+  }
+  CK(c, cudaEventRecord(c->ev[0], c->st));
+  CK(c, ensure(c, c->flags, 64));
+  CK(c, cudaMemsetAsync(c->flags.p, 0, 64, c->st));
+
+  // units and grid
+  int cpr = c->cells_per_rmax > 0 ? c->cells_per_rmax : 8;
+  Geom g{};
+  g.periodic = c->periodic;
+  g.nbins = c->nbins;
+  g.lmax = c->lmax;
+  uint32_t nc = 1;
+  if (c->periodic) {
+    c->unit = c->box / 4294967296.0;
+    g.shift = 32;
+    double ncd = std::floor(c->box * cpr / c->rmax);
+    nc = (uint32_t)std::max(1.0, std::min(ncd, 1024.0));
+    c->origin[0] = c->origin[1] = c->origin[2] = 0;
+  } else {
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    if (n > 0) {
+      int nblk = bbox_blocks(n);
+      CK(c, ensure(c, c->bbox_part, (size_t)nblk * 6 * sizeof(double)));
+      CK(c, launch_bbox(dxyz, n, P<double>(c->bbox_part), nblk, P<uint32_t>(c->flags), c->st));
+      std::vector<double> part((size_t)nblk * 6);
+      uint32_t fl = 0;
+      CK(c, cudaMemcpyAsync(part.data(), c->bbox_part.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->st));
+      CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaStreamSynchronize(c->st));
+      if (fl) return fail(c, CTB_ERR_NONFINITE, "non-finite coordinate in xyz");
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = INFINITY;
+        hi[k] = -INFINITY;
+      }
+      for (int b = 0; b < nblk; ++b)
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = std::min(lo[k], part[b * 6 + k]);
+          hi[k] = std::max(hi[k], part[b * 6 + 3 + k]);
+        }
+    }
+    double ext = 0;
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
+    if (!(ext > 0)) ext = c->rmax;
+    // the bounding cube spans at most 2^31 - 1024 units: int32 differences never overflow
+    c->unit = ext / (2147483648.0 - 1024.0);
+    for (int k = 0; k < 3; ++k) c->origin[k] = lo[k];
+    g.shift = 31;
+    double rmax_u = c->rmax / c->unit;
+    double ncd = std::ceil(2147483648.0 * cpr / rmax_u);
+    nc = (uint32_t)std::max(1.0, std::min(ncd, 1024.0));
+  }
+  g.nc = nc;
+  g.ncells = nc * nc * nc;
+  const double rmin_u = c->rmin / c->unit, rmax_u = c->rmax / c->unit;
+  g.rmin2_u = (float)(rmin_u * rmin_u);
+  g.rmax2_u = (float)(rmax_u * rmax_u);
+  g.rmin_u = (float)rmin_u;
+  g.inv_dr_u = (float)(c->nbins / (rmax_u - rmin_u));
+  g.cell_scale = (float)(nc / std::ldexp(1.0, g.shift));
+  g.rcell = (float)(rmax_u * nc / std::ldexp(1.0, g.shift) * (1.0 + 1e-5) + 1e-3);
+  c->g = g;
+
+  // buffers
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  CK(c, ensure(c, c->key0, nn * 4));
+  CK(c, ensure(c, c->val0, nn * 4));
+  CK(c, ensure(c, c->key1, nn * 4));
+  CK(c, ensure(c, c->val1, nn * 4));
+  CK(c, ensure(c, c->pts_in, nn * 16));
+  CK(c, ensure(c, c->pts, nn * 16));
+  CK(c, ensure(c, c->s2i, nn * 4));
+  CK(c, ensure(c, c->i2s, nn * 4));
+  CK(c, ensure(c, c->cell_start, ((size_t)g.ncells + 1) * 4));
+  const size_t hw = sort_hist_words(n);
+  CK(c, ensure(c, c->hist, hw * 4));
+  CK(c, ensure(c, c->scan_tmp, scan_tmp_words(hw) * 4));
+
+  IngestOut io{P<uint32_t>(c->key0), P<uint32_t>(c->val0), P<uint4>(c->pts_in)};
+  const double inv_unit = 1.0 / c->unit;
+  CK(c, launch_ingest(dxyz, dw, n, c->periodic ? c->box : 0.0, c->origin, inv_unit, g, io,
+                      P<uint32_t>(c->flags), c->st));
+  CK(c, cudaEventRecord(c->ev[1], c->st));
+  SortBufs sb{P<uint32_t>(c->key0), P<uint32_t>(c->val0), P<uint32_t>(c->key1), P<uint32_t>(c->val1),
+              P<uint32_t>(c->hist), P<uint32_t>(c->scan_tmp)};
+  bool in1 = false;
+  CK(c, radix_sort(sb, n, bits_for(g.ncells), &in1, c->st));
+  uint32_t* ks = in1 ? sb.k1 : sb.k0;
+  uint32_t* vs = in1 ? sb.v1 : sb.v0;
+  CK(c, launch_gather(vs, P<uint4>(c->pts_in), n, P<uint4>(c->pts), P<uint32_t>(c->s2i), P<uint32_t>(c->i2s),
+                      c->st));
+  CK(c, launch_cell_start(ks, n, g.ncells, P<uint32_t>(c->cell_start), c->st));
+  CK(c, cudaEventRecord(c->ev[2], c->st));
+  uint32_t fl = 0;
+  CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (fl) return fail(c, CTB_ERR_NONFINITE, "non-finite coordinate or weight");
+  c->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
+  c->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
+  for (int k = 2; k < kStages; ++k) c->t_ms[k] = 0;
+  c->n = n;
+  return CTB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pair kernel + contraction over a primary list (prim == NULL: all points)
+
+struct PairPlan {
+  int wpb, nblocks;
+  int64_t chunk;
+  int nparts;
+};
+
+int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
+  int wpb = c->wpb > 0 ? c->wpb : 4;
+  int bps = pair_max_blocks_per_sm(c->Lk, wpb);
+  if (bps < 1) return fail(c, CTB_ERR_CUDA, "pair kernel cannot be resident with this block size");
+  pl->wpb = wpb;
+  pl->nblocks = bps * c->nsm;
+  const size_t rowbytes = (size_t)c->nbins * c->lay.row * sizeof(float);
+  int64_t chunk = c->chunk > 0 ? c->chunk : (int64_t)((size_t)12 << 30) / (int64_t)rowbytes;
+  chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, std::max<int64_t>(np, 1)));
+  pl->chunk = chunk;
+  pl->nparts = 2 * c->nsm;
+  return CTB_OK;
+}
+
+int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, const PairPlan& pl, int* nchunks) {
+  const size_t listwords = (size_t)pl.nblocks * pl.wpb * c->nbins * c->cap;
+  CK(c, ensure(c, c->lists, listwords * 4));
+  CK(c, ensure(c, c->M, (size_t)pl.chunk * c->nbins * c->lay.row * sizeof(float)));
+  CK(c, ensure(c, c->wprim, (size_t)pl.chunk * sizeof(float)));
+  CK(c, ensure(c, c->counters, 64));
+  CK(c, cudaMemsetAsync(c->counters.p, 0, 64, c->st));
+  unsigned long long* work = P<unsigned long long>(c->counters);
+  unsigned long long* npairs = work + 1;
+  PairArgs a{};
+  a.pts = P<uint4>(c->pts);
+  a.cell_start = P<uint32_t>(c->cell_start);
+  a.prim = dprim;
+  a.M = P<float>(c->M);
+  a.wprim = P<float>(c->wprim);
+  a.lists = P<uint32_t>(c->lists);
+  a.cap = c->cap;
+  a.work = work;
+  a.npairs = npairs;
+  a.norm = P<float>(c->norm);
+  a.g = c->g;
+  a.row = c->lay.row;
+  std::memcpy(a.beta, c->beta, sizeof(a.beta));
+  int k = 0;
+  for (int64_t c0 = 0; c0 < np; c0 += pl.chunk, ++k) {
+    const int64_t cnt = std::min(pl.chunk, np - c0);
+    const int evk = std::min(k, kMaxChunkEvents - 1);
+    if (k > 0) CK(c, cudaMemsetAsync(work, 0, sizeof(unsigned long long), c->st));
+    a.prim_begin = c0;
+    a.prim_count = cnt;
+    CK(c, cudaEventRecord(c->ev[2 + 3 * evk], c->st));
+    CK(c, launch_pair(a, c->Lk, pl.wpb, pl.nblocks, c->st));
+    CK(c, cudaEventRecord(c->ev[3 + 3 * evk], c->st));
+    if (contract) {
+      ContractArgs ca{};
+      ca.M = P<float>(c->M);
+      ca.wprim = P<float>(c->wprim);
+      ca.np = cnt;
+      ca.nbins = c->nbins;
+      ca.lmax = c->lmax;
+      ca.row = c->lay.row;
+      ca.slot = P<int>(c->slot);
+      ca.partial = P<double>(c->partial);
+      ca.part0 = 0;
+      CK(c, launch_contract_fp32(ca, pl.nparts, c->st));
+    }
+    CK(c, cudaEventRecord(c->ev[4 + 3 * evk], c->st));
+  }
+  *nchunks = k;
+  return CTB_OK;
+}
+
+int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out) {
+  if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
+  if (!zeta_out) return fail(c, CTB_ERR_ARG, "zeta_out is NULL");
+  if (c->precision != CTB_PREC_FP32) return fail(c, CTB_ERR_UNSUPPORTED, "precision not available");
+  CK(c, cudaSetDevice(c->dev));
+  int r = ensure_tables(c);
+  if (r) return r;
+  PairPlan pl{};
+  r = plan_pairs(c, np, &pl);
+  if (r) return r;
+  const size_t zsz = (size_t)(c->lmax + 1) * c->nbins * c->nbins;
+  CK(c, ensure(c, c->partial, (size_t)pl.nparts * zsz * sizeof(double)));
+  CK(c, ensure(c, c->zeta, zsz * sizeof(double)));
+  CK(c, cudaMemsetAsync(c->partial.p, 0, (size_t)pl.nparts * zsz * sizeof(double), c->st));
+  int nchunks = 0;
+  const int evs = 2 + 3 * kMaxChunkEvents;
+  CK(c, cudaEventRecord(c->ev[evs], c->st));
+  r = run_pairs(c, dprim, np, true, pl, &nchunks);
+  if (r) return r;
+  CK(c, cudaEventRecord(c->ev[evs + 1], c->st));
+  CK(c, launch_finalize(P<double>(c->partial), pl.nparts, c->lmax, c->nbins, P<double>(c->zeta), c->st));
+  CK(c, cudaEventRecord(c->ev[evs + 2], c->st));
+  const bool dev_out = is_device_ptr(zeta_out);
+  CK(c, cudaMemcpyAsync(zeta_out, c->zeta.p, zsz * sizeof(double),
+                        dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  unsigned long long np_pairs = 0;
+  CK(c, cudaMemcpyAsync(&np_pairs, P<unsigned long long>(c->counters) + 1, sizeof(np_pairs),
+                        cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  c->npairs = np_pairs;
+  double tp = 0, tc = 0;
+  for (int k = 0; k < std::min(nchunks, kMaxChunkEvents); ++k) {
+    tp += elapsed(c->ev[2 + 3 * k], c->ev[3 + 3 * k]);
+    tc += elapsed(c->ev[3 + 3 * k], c->ev[4 + 3 * k]);
+  }
+  c->t_ms[0] = c->t_ms[1] = 0;
+  c->t_ms[2] = tp;
+  c->t_ms[3] = 0;
+  c->t_ms[4] = tc;
+  c->t_ms[5] = elapsed(c->ev[evs + 1], c->ev[evs + 2]);
+  return CTB_OK;
+}
+
+// catalogue indices (int64, host or device) -> sorted positions (uint32, device)
+__global__ void k_map_prim(const int64_t* __restrict__ idx, int64_t m, int64_t n, const uint32_t* __restrict__ i2s,
+                           uint32_t* __restrict__ out, uint32_t* flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v = idx[i];
+    if (v < 0 || v >= n) {
+      atomicOr(flags, 2u);
+      out[i] = 0;
+    } else {
+      out[i] = i2s[v];
+    }
+  }
+}
+
+int map_primaries(ctb_ctx* c, const int64_t* idx, int64_t m) {
+  if (m < 0) return fail(c, CTB_ERR_ARG, "negative primary count");
+  if (m > 0 && !idx) return fail(c, CTB_ERR_ARG, "primary_idx is NULL");
+  if (m == 0) return CTB_OK;
+  const int64_t* didx = idx;
+  if (!is_device_ptr(idx)) {
+    for (int64_t i = 0; i < m; ++i)
+      if (idx[i] < 0 || idx[i] >= c->n) return fail(c, CTB_ERR_ARG, "primary index out of range");
+    CK(c, ensure(c, c->idx64, (size_t)m * 8));
+    CK(c, cudaMemcpyAsync(c->idx64.p, idx, (size_t)m * 8, cudaMemcpyHostToDevice, c->st));
+    didx = P<int64_t>(c->idx64);
+  }
+  CK(c, ensure(c, c->prim, (size_t)m * 4));
+  CK(c, cudaMemsetAsync(c->flags.p, 0, 4, c->st));
+  int blocks = (int)std::min<int64_t>((m + 255) / 256, 65535);
+  k_map_prim<<<blocks, 256, 0, c->st>>>(didx, m, c->n, P<uint32_t>(c->i2s), P<uint32_t>(c->prim),
+                                        P<uint32_t>(c->flags));
+  ++g_launches;
+  CK(c, cudaGetLastError());
+  uint32_t fl = 0;
+  CK(c, cudaMemcpyAsync(&fl, c->flags.p, 4, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (fl & 2u) return fail(c, CTB_ERR_ARG, "primary index out of range");
+  return CTB_OK;
+}
+
+// M rows (slot layout) -> [m][nbins][(lmax+1)^2] in the l*l+l+m order
+__global__ void k_unpack_alm(const float* __restrict__ M, int64_t m, int nbins, int row, const int* __restrict__ slot,
+                             int nc, float* __restrict__ out) {
+  const int64_t total = m * nbins * nc;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(o % nc);
+    const int64_t pb = o / nc;
+    out[o] = M[pb * row + slot[c]];
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+const char* ctb_version(void) { return "ctb 0.1 (sm_103a)"; }
+
+ctb_ctx* ctb_create(double box, double r_min, double r_max, int nbins, int ell_max) {
+  if (!std::isfinite(box) || !std::isfinite(r_min) || !std::isfinite(r_max)) {
+    g_create_err = "non-finite argument";
+    return nullptr;
+  }
+  if (!(r_min >= 0) || !(r_max > r_min)) {
+    g_create_err = "need 0 <= r_min < r_max";
+    return nullptr;
+  }
+  if (nbins < 1 || nbins > CTB_NBINS_CAP) {
+    g_create_err = "nbins out of range [1, 64]";
+    return nullptr;
+  }
+  if (ell_max < 0 || ell_max > CTB_LMAX_CAP) {
+    g_create_err = "ell_max out of range [0, 20]";
+    return nullptr;
+  }
+  if (box > 0 && r_max > 0.5 * box) {
+    g_create_err = "periodic box needs r_max <= box/2";
+    return nullptr;
+  }
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    g_create_err = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return nullptr;
+  }
+  ctb_ctx* c = new ctb_ctx();
+  c->dev = dev;
+  c->nsm = nsm;
+  c->box = box;
+  c->rmin = r_min;
+  c->rmax = r_max;
+  c->nbins = nbins;
+  c->lmax = ell_max;
+  c->periodic = box > 0 ? 1 : 0;
+  return c;
+}
+
+void ctb_destroy(ctb_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  release_all(c);
+  cudaStreamSynchronize(c->st);
+  if (c->ev_ready)
+    for (auto& e : c->ev) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete c;
+}
+
+const char* ctb_last_error(const ctb_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int ctb_set_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
+  if (!c) return CTB_ERR_ARG;
+  const unsigned long long l0 = g_launches;
+  int r = load_points(c, xyz, w, n);
+  c->launches_points = g_launches - l0;
+  return r;
+}
+
+int ctb_compute(ctb_ctx* c, double* zeta_out) {
+  if (!c) return CTB_ERR_ARG;
+  if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
+  const unsigned long long l0 = g_launches;
+  int r = compute_impl(c, nullptr, c->n, zeta_out);
+  c->launches_compute = g_launches - l0;
+  return r;
+}
+
+int ctb_compute_subset(ctb_ctx* c, const int64_t* primary_idx, int64_t m, double* zeta_out) {
+  if (!c) return CTB_ERR_ARG;
+  if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
+  int r = map_primaries(c, primary_idx, m);
+  if (r) return r;
+  return compute_impl(c, m > 0 ? P<uint32_t>(c->prim) : nullptr, m, zeta_out);
+}
+
+int ctb_get_alm(ctb_ctx* c, const int64_t* primary_idx, int64_t m, float* alm_out) {
+  if (!c) return CTB_ERR_ARG;
+  if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
+  if (m > 0 && !alm_out) return fail(c, CTB_ERR_ARG, "alm_out is NULL");
+  int r = map_primaries(c, primary_idx, m);
+  if (r) return r;
+  if (m == 0) return CTB_OK;
+  r = ensure_tables(c);
+  if (r) return r;
+  PairPlan pl{};
+  r = plan_pairs(c, m, &pl);
+  if (r) return r;
+  pl.chunk = m;
+  int nch = 0;
+  r = run_pairs(c, P<uint32_t>(c->prim), m, false, pl, &nch);
+  if (r) return r;
+  const int nc = (c->lmax + 1) * (c->lmax + 1);
+  const size_t outsz = (size_t)m * c->nbins * nc;
+  const bool dev_out = is_device_ptr(alm_out);
+  float* dst = alm_out;
+  if (!dev_out) {
+    CK(c, ensure(c, c->alm, outsz * 4));
+    dst = P<float>(c->alm);
+  }
+  int blocks = (int)std::min<size_t>((outsz + 255) / 256, 65535);
+  k_unpack_alm<<<blocks, 256, 0, c->st>>>(P<float>(c->M), m, c->nbins, c->lay.row, P<int>(c->slot), nc, dst);
+  ++g_launches;
+  CK(c, cudaGetLastError());
+  if (!dev_out) CK(c, cudaMemcpyAsync(alm_out, dst, outsz * 4, cudaMemcpyDeviceToHost, c->st));
+  unsigned long long np_pairs = 0;
+  CK(c, cudaMemcpyAsync(&np_pairs, P<unsigned long long>(c->counters) + 1, sizeof(np_pairs),
+                        cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  c->npairs = np_pairs;
+  return CTB_OK;
+}
+
+int ctb_compute_batch(ctb_ctx* c, const double* const* xyz, const double* const* w, const int64_t* n, int k,
+                      double* zeta_out) {
+  if (!c) return CTB_ERR_ARG;
+  return fail(c, CTB_ERR_UNSUPPORTED, "batch mode not available in this build");
+  (void)xyz;
+  (void)w;
+  (void)n;
+  (void)k;
+  (void)zeta_out;
+}
+
+int ctb_set_option(ctb_ctx* c, int key, int64_t v) {
+  if (!c) return CTB_ERR_ARG;
+  switch (key) {
+    case CTB_OPT_PRECISION:
+      if (v != CTB_PREC_FP32 && v != CTB_PREC_BF16X3 && v != CTB_PREC_TF32)
+        return fail(c, CTB_ERR_ARG, "unknown precision");
+      if (v != CTB_PREC_FP32) return fail(c, CTB_ERR_UNSUPPORTED, "precision not available in this build");
+      c->precision = (int)v;
+      return CTB_OK;
+    case CTB_OPT_CELLS_PER_RMAX:
+      if (v < 0 || v > 64) return fail(c, CTB_ERR_ARG, "cells per r_max out of range [0, 64]");
+      c->cells_per_rmax = (int)v;
+      c->n = -1;  // grid changes: the catalogue must be reloaded
+      return CTB_OK;
+    case CTB_OPT_BIN_CAPACITY:
+      if (v < 256 || v > 65536) return fail(c, CTB_ERR_ARG, "bin capacity out of range [256, 65536]");
+      c->cap = (uint32_t)((v + 3) & ~3);
+      return CTB_OK;
+    case CTB_OPT_WARPS_PER_BLOCK:
+      if (v < 0 || v > 16) return fail(c, CTB_ERR_ARG, "warps per block out of range [0, 16]");
+      c->wpb = (int)v;
+      return CTB_OK;
+    case CTB_OPT_CHUNK_PRIMARIES:
+      if (v != 0 && v < 1024) return fail(c, CTB_ERR_ARG, "chunk must be 0 or >= 1024");
+      c->chunk = v;
+      return CTB_OK;
+    case CTB_OPT_DETERMINISTIC:
+      if (v != 0 && v != 1) return fail(c, CTB_ERR_ARG, "deterministic must be 0 or 1");
+      c->deterministic = (int)v;
+      return CTB_OK;
+    default:
+      return fail(c, CTB_ERR_ARG, "unknown option key");
+  }
+}
+
+int ctb_set_stream(ctb_ctx* c, void* stream) {
+  if (!c) return CTB_ERR_ARG;
+  c->st = static_cast<cudaStream_t>(stream);
+  return CTB_OK;
+}
+
+int ctb_set_allocator(ctb_ctx* c, void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* user) {
+  if (!c) return CTB_ERR_ARG;
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(c, CTB_ERR_ARG, "alloc and free must both be set");
+  cudaSetDevice(c->dev);
+  release_all(c);
+  cudaStreamSynchronize(c->st);
+  c->alloc_fn = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  c->n = -1;
+  return CTB_OK;
+}
+
+int ctb_get_timings(ctb_ctx* c, double* ms, int cap) {
+  if (!c || (cap > 0 && !ms)) return CTB_ERR_ARG;
+  int k = std::min(cap, kStages);
+  for (int i = 0; i < k; ++i) ms[i] = c->t_ms[i];
+  return k;
+}
+
+int ctb_get_launch_count(ctb_ctx* c, uint64_t* kernels) {
+  if (!c || !kernels) return CTB_ERR_ARG;
+  *kernels = c->launches_points + c->launches_compute;
+  return CTB_OK;
+}
+
+int ctb_get_pair_count(ctb_ctx* c, uint64_t* pairs) {
+  if (!c || !pairs) return CTB_ERR_ARG;
+  *pairs = c->npairs;
+  return CTB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// ctb_internal.cuh -- shared declarations of the libctb CUDA implementation.
+//
+// Point representation on the device (one uint4 per point, 16 B):
+//   x, y, z : unsigned 32-bit fixed-point coordinates.  Periodic cube: the
+//             side L maps onto 2^32 units, so the wrapped difference of two
+//             coordinates read as int32 IS the minimum-image separation.
+//             Open space: the bounding cube maps onto [0, 2^31) units, so a
+//             difference never overflows int32.
+//   w       : float32 weight bits.
+// One unit is L / 2^32 (about 2.3e-7 for L = 1000), so quantisation moves a
+// point by far less than float32 rounding of a separation does.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ctb.h"
+
+namespace ctb {
+
+constexpr int kLmaxCap = CTB_LMAX_CAP;
+constexpr int kNbinsCap = CTB_NBINS_CAP;
+constexpr int kWarp = 32;
+// coefficients accumulated per pass of the pair kernel (register budget)
+constexpr int kPassCap = 128;
+
+// ---------------------------------------------------------------------------
+// grid / estimator geometry shared by the kernels
+
+struct Geom {
+  int periodic;        // 1: periodic cube, 0: open space
+  int shift;           // 32 (periodic) or 31 (open): unit coordinates < 2^shift
+  uint32_t nc;         // cells per axis
+  uint32_t ncells;     // nc^3
+  int nbins;
+  int lmax;            // requested ell_max
+  float rmin2_u;       // r_min^2 in units^2
+  float rmax2_u;       // r_max^2 in units^2
+  float rmin_u;        // r_min in units
+  float inv_dr_u;      // nbins / (r_max - r_min) in 1/units
+  float rcell;         // r_max in cell units, padded by a small slack
+  float cell_scale;    // nc / 2^shift : units -> cell units
+};
+
+// ---------------------------------------------------------------------------
+// real-harmonic coefficient layout of one pair-kernel configuration
+//
+// The pair kernel accumulates the (l, m) coefficients in passes over m ranges
+// [m0, m1] (one pass when ell_max <= 10).  Within a pass the slots run over
+// l = m0..L, and for each l over m = -min(l,m1)..-m0, (0), m0..min(l,m1).
+// Pass p occupies slots [base_p, base_p + ncp_p) of a row, ncp_p the pass's
+// coefficient count rounded up to a multiple of 32.
+
+__host__ __device__ constexpr int coef_count(int L, int m0, int m1) {
+  int s = 0;
+  for (int m = m0; m <= m1 && m <= L; ++m) s += (L - m + 1) * (m == 0 ? 1 : 2);
+  return s;
+}
+
+__host__ __device__ constexpr int pass_end(int L, int m0, int cap) {
+  int s = 0, m = m0;
+  while (m <= L) {
+    int c = (L - m + 1) * (m == 0 ? 1 : 2);
+    if (s + c > cap && m > m0) break;
+    s += c;
+    ++m;
+  }
+  return m - 1;
+}
+
+__host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
+
+__host__ __device__ constexpr int n_in_l(int l, int m0, int m1) {
+  int hi = l < m1 ? l : m1;
+  if (hi < m0) return 0;
+  int k = hi - m0 + 1;
+  return m0 == 0 ? 2 * k - 1 : 2 * k;
+}
+
+__host__ __device__ constexpr int l_base(int l, int m0, int m1) {
+  int s = 0;
+  for (int q = 0; q < l; ++q) s += n_in_l(q, m0, m1);
+  return s;
+}
+
+// slot of (l, m) inside the pass [m0, m1] (requires m0 <= |m| <= min(l, m1))
+__host__ __device__ constexpr int local_slot(int l, int m, int m0, int m1) {
+  int hi = l < m1 ? l : m1;
+  if (m0 == 0) return l_base(l, m0, m1) + (m + hi);
+  if (m < 0) return l_base(l, m0, m1) + (m + hi);
+  return l_base(l, m0, m1) + (hi - m0 + 1) + (m - m0);
+}
+
+// pair-kernel instantiation that serves a requested ell_max
+__host__ __device__ constexpr int lmax_kernel(int lmax) {
+  return lmax <= 10 ? lmax : (lmax + 1) / 2 * 2;
+}
+
+// Host-side description of the row layout for a kernel L.
+struct Layout {
+  int L;                         // kernel ell_max
+  int npass;
+  int m0[kLmaxCap + 1], m1[kLmaxCap + 1], base[kLmaxCap + 1], ncp[kLmaxCap + 1];
+  int row;                       // floats per (primary, bin) row
+  // slot of coefficient index l*l + l + m for l <= L
+  int slot[(kLmaxCap + 1) * (kLmaxCap + 1)];
+};
+void make_layout(int L, Layout* out);
+
+// kernels launched by this host thread (every launcher adds its launches)
+extern thread_local unsigned long long g_launches;
+
+// recurrence constants (pair_dispatch.cu)
+void fill_beta(float* beta);   // beta_lm at [l*(kLmaxCap+1)+m]
+double norm_lm(int l, int m);  // C_lm of the real orthonormal Y_l,m
+
+// ---------------------------------------------------------------------------
+// kernels and launchers (all asynchronous on `st`)
+
+// grid.cu
+struct IngestOut {
+  uint32_t* key;    // cell key per point (input order)
+  uint32_t* val;    // input index
+  uint4* pts;       // fixed-point point per input index
+};
+// box > 0: periodic; else origin/inv_unit map into [0, 2^31)
+cudaError_t launch_ingest(const double* xyz, const double* w, int64_t n, double box,
+                          const double* origin3, double inv_unit, const Geom& g,
+                          IngestOut out, uint32_t* d_flags, cudaStream_t st);
+cudaError_t launch_bbox(const double* xyz, int64_t n, double* d_part, int nblk,
+                        uint32_t* d_flags, cudaStream_t st);
+int bbox_blocks(int64_t n);
+
+// radix sort of (key, val), key < 2^bits; returns the buffers holding the result
+struct SortBufs {
+  uint32_t *k0, *v0, *k1, *v1;
+  uint32_t* hist;       // [256 * nblk]
+  uint32_t* scan_tmp;   // scan workspace
+};
+int sort_blocks(int64_t n);
+size_t sort_hist_words(int64_t n);
+size_t scan_tmp_words(size_t len);
+cudaError_t radix_sort(SortBufs& b, int64_t n, int bits, bool* result_in_1, cudaStream_t st);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, size_t len,
+                               uint32_t* tmp, cudaStream_t st);
+
+cudaError_t launch_gather(const uint32_t* val_sorted, const uint4* pts_in, int64_t n,
+                          uint4* pts_sorted, uint32_t* sorted_to_input,
+                          uint32_t* input_to_sorted, cudaStream_t st);
+cudaError_t launch_cell_start(const uint32_t* key_sorted, int64_t n, uint32_t ncells,
+                              uint32_t* cell_start, cudaStream_t st);
+
+// pair.cu
+struct PairArgs {
+  const uint4* pts;           // sorted points
+  const uint32_t* cell_start; // [ncells + 1]
+  const uint32_t* prim;       // sorted positions of the primaries (NULL: identity)
+  int64_t prim_begin;         // first primary of this launch (index into prim / positions)
+  int64_t prim_count;         // primaries in this launch
+  float* M;                   // [prim_count][nbins][row] coefficient rows
+  float* wprim;               // [prim_count] primary weights
+  uint32_t* lists;            // per-warp neighbour lists [warps][nbins][cap]
+  uint32_t cap;               // list capacity per bin (multiple of 4, >= 64)
+  unsigned long long* work;   // work counter (zeroed before launch)
+  unsigned long long* npairs; // binned-pair counter (accumulated)
+  const float* norm;          // [row] normalisation per slot
+  Geom g;
+  int row;                    // floats per (primary, bin) row
+  float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];  // recurrence beta_lm at [l*(kLmaxCap+1)+m]
+};
+int pair_max_blocks_per_sm(int lmax_kernel, int warps_per_block);
+cudaError_t launch_pair(const PairArgs& a, int lmax_kernel, int warps_per_block, int nblocks,
+                        cudaStream_t st);
+
+// contract.cu
+struct ContractArgs {
+  const float* M;          // [np][nbins][row]
+  const float* wprim;      // [np]
+  int64_t np;
+  int nbins;
+  int lmax;
+  int row;
+  const int* slot;         // device copy of Layout::slot
+  double* partial;         // [nparts][(lmax+1)][nbins][nbins] (upper triangle used)
+  int part0;               // first partial row this launch writes
+};
+cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t st);
+cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbins,
+                            double* zeta, cudaStream_t st);
+
+}  // namespace ctb

@@ -1,0 +1,9 @@
+// pair_c.cu -- explicit instantiations of the pair-multipole kernel (see pair.cuh).
+#include "pair.cuh"
+
+namespace ctb {
+template cudaError_t launch_pair_L<9>(const PairArgs&, int, int, cudaStream_t);
+template int pair_occupancy_L<9>(int);
+template cudaError_t launch_pair_L<10>(const PairArgs&, int, int, cudaStream_t);
+template int pair_occupancy_L<10>(int);
+}  // namespace ctb

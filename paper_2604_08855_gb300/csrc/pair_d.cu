@@ -1,0 +1,9 @@
+// pair_d.cu -- explicit instantiations of the pair-multipole kernel (see pair.cuh).
+#include "pair.cuh"
+
+namespace ctb {
+template cudaError_t launch_pair_L<12>(const PairArgs&, int, int, cudaStream_t);
+template int pair_occupancy_L<12>(int);
+template cudaError_t launch_pair_L<14>(const PairArgs&, int, int, cudaStream_t);
+template int pair_occupancy_L<14>(int);
+}  // namespace ctb

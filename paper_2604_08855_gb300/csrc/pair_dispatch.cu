@@ -1,0 +1,96 @@
+// pair_dispatch.cu -- coefficient layout, recurrence constants, and the
+// ell_max dispatch of the pair-multipole kernel.
+#include <cmath>
+
+#include "ctb_internal.cuh"
+
+namespace ctb {
+
+// explicit instantiations live in pair_[a-f].cu
+template <int L>
+cudaError_t launch_pair_L(const PairArgs&, int, int, cudaStream_t);
+template <int L>
+int pair_occupancy_L(int);
+
+void make_layout(int L, Layout* out) {
+  Layout& y = *out;
+  y.L = L;
+  y.npass = 0;
+  int base = 0;
+  for (int i = 0; i < (kLmaxCap + 1) * (kLmaxCap + 1); ++i) y.slot[i] = -1;
+  for (int m0 = 0; m0 <= L;) {
+    int m1 = pass_end(L, m0, kPassCap);
+    int ncp = round32(coef_count(L, m0, m1));
+    y.m0[y.npass] = m0;
+    y.m1[y.npass] = m1;
+    y.base[y.npass] = base;
+    y.ncp[y.npass] = ncp;
+    for (int l = m0; l <= L; ++l) {
+      int hi = l < m1 ? l : m1;
+      for (int m = -hi; m <= hi; ++m) {
+        int am = m < 0 ? -m : m;
+        if (am < m0) continue;
+        y.slot[l * l + l + m] = base + local_slot(l, m, m0, m1);
+      }
+    }
+    base += ncp;
+    ++y.npass;
+    m0 = m1 + 1;
+  }
+  y.row = base;
+}
+
+// a_lm = sqrt((4l^2-1)/(l^2-m^2)),  b_lm = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)):
+// the normalised associated-Legendre recurrence  Pbar_l = a (z Pbar_{l-1} - b Pbar_{l-2}).
+static double rec_a(int l, int m) { return std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m)); }
+static double rec_b(int l, int m) {
+  return std::sqrt((((double)(l - 1) * (l - 1)) - (double)m * m) / (4.0 * (l - 1) * (l - 1) - 1.0));
+}
+
+// Monic form p_l = z p_{l-1} - beta p_{l-2}:  beta_lm = b_lm / a_{l-1,m}.
+void fill_beta(float* beta) {
+  for (int i = 0; i < (kLmaxCap + 1) * (kLmaxCap + 1); ++i) beta[i] = 0.f;
+  for (int m = 0; m <= kLmaxCap; ++m)
+    for (int l = m + 2; l <= kLmaxCap; ++l) beta[l * (kLmaxCap + 1) + m] = (float)(rec_b(l, m) / rec_a(l - 1, m));
+}
+
+// Normalisation C_lm turning the monic p_l^m times Re/Im (x+iy)^m into the
+// real orthonormal Y_l,+-m (Condon-Shortley phase and sqrt 2 for m != 0):
+//   C_mm = (-1)^m / sqrt(4 pi) prod_{k=1..m} sqrt((2k+1)/(2k)),
+//   C_lm = C_mm prod_{k=m+1..l} a_km.
+double norm_lm(int l, int m) {
+  int am = m < 0 ? -m : m;
+  double c = 1.0 / std::sqrt(4.0 * M_PI);
+  for (int k = 1; k <= am; ++k) c *= -std::sqrt((2.0 * k + 1.0) / (2.0 * k));
+  for (int k = am + 1; k <= l; ++k) c *= rec_a(k, am);
+  if (am != 0) c *= M_SQRT2;
+  return c;
+}
+
+int pair_max_blocks_per_sm(int L, int wpb) {
+  switch (L) {
+#define CASE(X) \
+  case X:       \
+    return pair_occupancy_L<X>(wpb);
+    CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
+    CASE(12) CASE(14) CASE(16) CASE(18) CASE(20)
+#undef CASE
+    default:
+      return 0;
+  }
+}
+
+cudaError_t launch_pair(const PairArgs& a, int L, int wpb, int nblocks, cudaStream_t st) {
+  switch (L) {
+#define CASE(X) \
+  case X:       \
+    return launch_pair_L<X>(a, wpb, nblocks, st);
+    CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
+    CASE(12) CASE(14) CASE(16) CASE(18) CASE(20)
+#undef CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ctb

@@ -1,0 +1,235 @@
+"""Thin ctypes binding to libctb (include/ctb.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module converts
+numpy arrays / torch tensors to pointers and status codes to exceptions.  It
+raises ImportError when the library has not been built: there is no CPU
+fallback.
+
+    from paper_2604_08855_gb300.ctb import CTB
+    est = CTB(box=1000.0, rmin=5.0, rmax=200.0, nbins=20, lmax=10)
+    est.set_points(xyz, w)            # numpy (host) or torch CUDA tensors
+    zeta = est.compute()              # numpy float64 [(lmax+1), nbins, nbins]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libctb.so")
+
+OK = 0
+ERR_ARG, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+OPT_PRECISION, OPT_CELLS_PER_RMAX, OPT_BIN_CAPACITY, OPT_WARPS_PER_BLOCK, OPT_CHUNK_PRIMARIES, \
+    OPT_DETERMINISTIC = 1, 2, 3, 4, 5, 6
+PREC_FP32, PREC_BF16X3, PREC_TF32 = 0, 1, 2
+LMAX_CAP, NBINS_CAP = 20, 64
+
+# every symbol include/ctb.h declares
+EXPORTS = ("ctb_create", "ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm",
+           "ctb_compute_batch", "ctb_set_option", "ctb_set_stream", "ctb_set_allocator",
+           "ctb_get_timings", "ctb_get_pair_count", "ctb_get_launch_count", "ctb_destroy", "ctb_last_error",
+           "ctb_version")
+
+_lib = None
+
+
+class CTBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load libctb.so (ImportError if it is missing; build it with build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libctb.so not built at {path}: run paper_2604_08855_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.ctb_create.argtypes = [d, d, d, i32, i32]
+    lib.ctb_create.restype = vp
+    lib.ctb_set_points.argtypes = [vp, vp, vp, i64]
+    lib.ctb_compute.argtypes = [vp, vp]
+    lib.ctb_compute_subset.argtypes = [vp, vp, i64, vp]
+    lib.ctb_get_alm.argtypes = [vp, vp, i64, vp]
+    lib.ctb_compute_batch.argtypes = [vp, vp, vp, vp, i32, vp]
+    lib.ctb_set_option.argtypes = [vp, i32, i64]
+    lib.ctb_set_stream.argtypes = [vp, vp]
+    lib.ctb_set_allocator.argtypes = [vp, vp, vp, vp]
+    lib.ctb_get_timings.argtypes = [vp, vp, i32]
+    lib.ctb_get_pair_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.ctb_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.ctb_destroy.argtypes = [vp]
+    lib.ctb_destroy.restype = None
+    lib.ctb_last_error.argtypes = [vp]
+    lib.ctb_last_error.restype = ctypes.c_char_p
+    lib.ctb_version.argtypes = []
+    lib.ctb_version.restype = ctypes.c_char_p
+    for name in ("ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm", "ctb_compute_batch",
+                 "ctb_set_option", "ctb_set_stream", "ctb_set_allocator", "ctb_get_timings",
+                 "ctb_get_pair_count", "ctb_get_launch_count"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (host or CUDA), or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _as_f64(x, shape_tail=None):
+    if x is None or hasattr(x, "data_ptr"):
+        if x is not None:
+            import torch
+            if x.dtype != torch.float64 or not x.is_contiguous():
+                raise TypeError("torch inputs must be contiguous float64")
+        return x
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+class CTB:
+    """One estimator configuration on the current CUDA device."""
+
+    def __init__(self, box: float, rmin: float, rmax: float, nbins: int, lmax: int):
+        self.lib = load()
+        self.box, self.rmin, self.rmax, self.nbins, self.lmax = float(box), float(rmin), float(rmax), int(nbins), int(lmax)
+        h = self.lib.ctb_create(self.box, self.rmin, self.rmax, self.nbins, self.lmax)
+        if not h:
+            raise CTBError(ERR_ARG, self.lib.ctb_last_error(None).decode())
+        self._h = ctypes.c_void_p(h)
+        self.n = None
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.ctb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc):
+        if rc < 0:
+            raise CTBError(rc, self.lib.ctb_last_error(self._h).decode())
+        return rc
+
+    @property
+    def zeta_shape(self):
+        return (self.lmax + 1, self.nbins, self.nbins)
+
+    def set_option(self, key: int, value: int):
+        self._check(self.lib.ctb_set_option(self._h, int(key), int(value)))
+
+    def set_stream(self, stream):
+        """stream: torch.cuda.Stream, an integer cudaStream_t, or None."""
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._check(self.lib.ctb_set_stream(self._h, ctypes.c_void_p(stream or 0)))
+
+    def use_torch_allocator(self, device=None):
+        """Route device allocations through torch's caching allocator."""
+        import torch
+        dev = torch.cuda.current_device() if device is None else int(device)
+        AF = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+        FF = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+        def _alloc(nbytes, _user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev)
+            except Exception:
+                return None
+
+        def _free(ptr, _user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        af, ff = AF(_alloc), FF(_free)
+        self._keep = [af, ff]
+        self._check(self.lib.ctb_set_allocator(self._h, ctypes.cast(af, ctypes.c_void_p),
+                                               ctypes.cast(ff, ctypes.c_void_p), None))
+
+    def set_points(self, xyz, w=None):
+        xyz = _as_f64(xyz)
+        w = _as_f64(w)
+        n = int(xyz.shape[0])
+        if tuple(xyz.shape[1:]) != (3,):
+            raise ValueError("xyz must be (n, 3)")
+        if w is not None and tuple(w.shape) != (n,):
+            raise ValueError("w must be (n,)")
+        self._check(self.lib.ctb_set_points(self._h, _ptr(xyz), _ptr(w), n))
+        self.n = n
+
+    def _out(self, out, shape, dtype):
+        if out is None:
+            return np.zeros(shape, dtype=dtype)
+        return out
+
+    def compute(self, out=None):
+        z = self._out(out, self.zeta_shape, np.float64)
+        self._check(self.lib.ctb_compute(self._h, _ptr(z)))
+        return z
+
+    def compute_subset(self, primaries, out=None):
+        p = primaries if hasattr(primaries, "data_ptr") else np.ascontiguousarray(primaries, dtype=np.int64)
+        z = self._out(out, self.zeta_shape, np.float64)
+        self._check(self.lib.ctb_compute_subset(self._h, _ptr(p), int(p.shape[0]), _ptr(z)))
+        return z
+
+    def get_alm(self, primaries, out=None):
+        p = primaries if hasattr(primaries, "data_ptr") else np.ascontiguousarray(primaries, dtype=np.int64)
+        a = self._out(out, (int(p.shape[0]), self.nbins, (self.lmax + 1) ** 2), np.float32)
+        self._check(self.lib.ctb_get_alm(self._h, _ptr(p), int(p.shape[0]), _ptr(a)))
+        return a
+
+    def compute_batch(self, cats, out=None):
+        """cats: list of (xyz, w) pairs (numpy or torch); returns [k, lmax+1, nbins, nbins]."""
+        k = len(cats)
+        xs = [_as_f64(c[0]) for c in cats]
+        ws = [_as_f64(c[1]) if len(c) > 1 else None for c in cats]
+        xp = (ctypes.c_void_p * k)(*[_ptr(x).value for x in xs])
+        wp = (ctypes.c_void_p * k)(*[(_ptr(w).value if w is not None else None) for w in ws])
+        ns = np.ascontiguousarray([x.shape[0] for x in xs], dtype=np.int64)
+        z = self._out(out, (k,) + self.zeta_shape, np.float64)
+        self._check(self.lib.ctb_compute_batch(self._h, ctypes.cast(xp, ctypes.c_void_p),
+                                               ctypes.cast(wp, ctypes.c_void_p), _ptr(ns), k, _ptr(z)))
+        return z
+
+    def timings(self):
+        """ms per stage: ingest, sort+grid, pair, pack, contraction, reduce."""
+        buf = (ctypes.c_double * 6)()
+        k = self._check(self.lib.ctb_get_timings(self._h, ctypes.cast(buf, ctypes.c_void_p), 6))
+        return list(buf)[:k]
+
+    def launch_count(self) -> int:
+        """Kernels launched by the last set_points plus the last compute."""
+        v = ctypes.c_uint64(0)
+        self._check(self.lib.ctb_get_launch_count(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def pair_count(self) -> int:
+        v = ctypes.c_uint64(0)
+        self._check(self.lib.ctb_get_pair_count(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+
+def version() -> str:
+    return load().ctb_version().decode()

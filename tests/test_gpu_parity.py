@@ -1,0 +1,225 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Tolerance (FP32 pair kernel + FP32 contraction + FP64 reduction): 1e-5 on
+the Gram-normalised metric of tests/parity.py, the FP32-mode bound the
+estimator's accuracy target sets.  Inputs are the seeded synthetic
+catalogues of paper_2604_08855_gb300.synth.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_08855_gb300 import synth
+from tests.parity import alm_err, zeta_err
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctbmod():
+    from paper_2604_08855_gb300 import build
+    build.build()
+    from paper_2604_08855_gb300 import ctb
+    return ctb
+
+
+def make(ctbmod, box, rmin, rmax, nbins, lmax, **opts):
+    est = ctbmod.CTB(box, rmin, rmax, nbins, lmax)
+    for k, v in opts.items():
+        est.set_option(getattr(ctbmod, "OPT_" + k.upper()), v)
+    return est
+
+
+def run_full(ctbmod, xyz, w, kw, **opts):
+    est = make(ctbmod, **kw, **opts)
+    est.set_points(xyz, w)
+    z = est.compute()
+    return z, est
+
+
+# ----------------------------------------------------------------- small cases
+
+
+@pytest.mark.parametrize("box", [400.0, 0.0])
+@pytest.mark.parametrize("lmax", [0, 3, 10])
+def test_small_thomas_vs_oracle(ctbmod, box, lmax):
+    xyz, w = synth.thomas(4000, 400.0, 40, 5.0, seed=21, weights="u0.5-1.5")
+    kw = dict(box=box, rmin=2.0, rmax=60.0, nbins=7, lmax=lmax)
+    z, est = run_full(ctbmod, xyz, w, kw)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+def test_uniform_20k_full_vs_oracle(ctbmod):
+    """20,000 uniform points, L = 1000, r in [10, 100], 10 bins, l_max = 10."""
+    xyz, w = synth.uniform_20k()
+    kw = synth.config_params(1)
+    z, est = run_full(ctbmod, xyz, w, kw)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+@pytest.mark.parametrize("lmax", [12, 20])
+def test_multipass_lmax_vs_oracle(ctbmod, lmax):
+    xyz, w = synth.thomas(3000, 300.0, 30, 5.0, seed=23, weights="u0.5-1.5")
+    kw = dict(box=300.0, rmin=3.0, rmax=50.0, nbins=5, lmax=lmax)
+    z, est = run_full(ctbmod, xyz, w, kw)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+def test_alm_vs_oracle(ctbmod):
+    xyz, w = synth.thomas(5000, 300.0, 50, 5.0, seed=24, weights="u0.5-1.5")
+    kw = dict(box=300.0, rmin=2.0, rmax=45.0, nbins=6, lmax=10)
+    est = make(ctbmod, **kw)
+    est.set_points(xyz, w)
+    prim = synth.sample_primaries(xyz.shape[0], 64, seed=3)
+    a = est.get_alm(prim)
+    a_ref = oracle.alm(xyz, w, prim=prim, **kw)
+    w2 = oracle.alm(xyz, w * w, prim=prim, **{**kw, "lmax": 0})[:, :, 0] * np.sqrt(4 * np.pi)
+    assert alm_err(a, a_ref, w2, 10) < TOL_FP32
+
+
+@pytest.mark.parametrize("cap", [256, 4096])
+@pytest.mark.parametrize("cpr", [1, 3, 16])
+def test_grid_and_list_capacity_do_not_change_result(ctbmod, cap, cpr):
+    """Cell size and per-bin list capacity (overflow -> several runs per bin)."""
+    xyz, w = synth.thomas(6000, 200.0, 30, 4.0, seed=25, weights="u0.5-1.5")
+    kw = dict(box=200.0, rmin=1.0, rmax=40.0, nbins=4, lmax=4)
+    z, _ = run_full(ctbmod, xyz, w, kw, bin_capacity=cap, cells_per_rmax=cpr)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+def test_subset_and_partition(ctbmod):
+    xyz, w = synth.thomas(5000, 300.0, 50, 5.0, seed=26, weights="u0.5-1.5")
+    kw = dict(box=300.0, rmin=2.0, rmax=50.0, nbins=6, lmax=6)
+    est = make(ctbmod, **kw)
+    est.set_points(xyz, w)
+    zfull = est.compute()
+    perm = np.random.default_rng(0).permutation(xyz.shape[0])
+    parts = [perm[:1000], perm[1000:3500], perm[3500:]]
+    zs = [est.compute_subset(p) for p in parts]
+    ref = oracle.zeta(xyz, w, prim=parts[0], **kw)
+    assert zeta_err(zs[0], ref) < TOL_FP32
+    reff = oracle.zeta(xyz, w, **kw)
+    assert zeta_err(sum(zs), reff) < TOL_FP32
+    assert zeta_err(zfull, reff) < TOL_FP32
+
+
+# ------------------------------------------------------------------ edge cases
+
+
+def test_edge_empty_and_single(ctbmod):
+    kw = dict(box=100.0, rmin=1.0, rmax=20.0, nbins=3, lmax=4)
+    est = make(ctbmod, **kw)
+    est.set_points(np.zeros((0, 3)), None)
+    assert np.all(est.compute() == 0)
+    est.set_points(np.array([[5.0, 5.0, 5.0]]), np.array([2.0]))
+    assert np.all(est.compute() == 0)
+    assert est.pair_count() == 0
+
+
+def test_edge_hand_triangle_and_faces(ctbmod):
+    """O with neighbours at 120 degrees in bins 0 and 1, placed across the
+    periodic faces: zeta_l(0,1) = wO wA wB P_l(-1/2)."""
+    from numpy.polynomial import legendre as npleg
+    t = np.deg2rad(120.0)
+    O = np.array([0.2, 99.9, 50.0])
+    pts = np.array([O, O + [15.0, 0, 0], O + [25 * np.cos(t), 25 * np.sin(t), 0]]) % 100.0
+    w = np.array([1.3, 0.7, -0.4])
+    kw = dict(box=100.0, rmin=10.0, rmax=30.0, nbins=2, lmax=10)
+    z, _ = run_full(ctbmod, pts, w, kw)
+    for l in range(11):
+        c = np.zeros(l + 1)
+        c[l] = 1
+        assert abs(z[l, 0, 1] - 1.3 * 0.7 * -0.4 * npleg.legval(-0.5, c)) < 1e-5
+
+
+def test_edge_all_in_one_cell_nbins1_rmin0(ctbmod):
+    rng = np.random.default_rng(3)
+    xyz = 50.0 + rng.uniform(-1, 1, size=(300, 3))
+    w = rng.uniform(0.5, 1.5, 300)
+    kw = dict(box=0.0, rmin=0.0, rmax=4.0, nbins=1, lmax=6)
+    z, _ = run_full(ctbmod, xyz, w, kw)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+def test_edge_coincident_points_and_small_box(ctbmod):
+    """Duplicated points (r = 0 never binned) in a box only a few cells wide."""
+    rng = np.random.default_rng(4)
+    base = rng.uniform(0, 10.0, size=(200, 3))
+    xyz = np.concatenate([base, base[:50]])
+    w = rng.uniform(0.5, 1.5, xyz.shape[0])
+    kw = dict(box=10.0, rmin=0.0, rmax=5.0, nbins=3, lmax=5)
+    z, _ = run_full(ctbmod, xyz, w, kw)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+def test_edge_negative_weights_and_wrap_inputs(ctbmod):
+    xyz, _ = synth.uniform(3000, 200.0, seed=9)
+    xyz = xyz + np.array([-200.0, 400.0, -600.0])  # periodic images of the same catalogue
+    w = np.random.default_rng(9).uniform(-1.0, 1.0, xyz.shape[0])
+    kw = dict(box=200.0, rmin=2.0, rmax=30.0, nbins=5, lmax=8)
+    z, _ = run_full(ctbmod, xyz, w, kw)
+    ref = oracle.zeta(np.mod(xyz, 200.0), w, **kw)
+    # negative primary weights: the Gram bound still scales every entry
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+def test_errors_are_status_codes(ctbmod):
+    with pytest.raises(ctbmod.CTBError):
+        ctbmod.CTB(100.0, 1.0, 60.0, 4, 2)           # r_max > L/2
+    with pytest.raises(ctbmod.CTBError):
+        ctbmod.CTB(100.0, 1.0, 10.0, 4, 21)          # l_max above the cap
+    est = ctbmod.CTB(100.0, 1.0, 10.0, 4, 2)
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.compute()
+    assert e.value.code == ctbmod.ERR_STATE
+    bad = np.zeros((10, 3))
+    bad[3, 1] = np.nan
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.set_points(bad)
+    assert e.value.code == ctbmod.ERR_NONFINITE
+    est.set_points(np.zeros((4, 3)))
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.compute_subset(np.array([0, 7]))
+    assert e.value.code == ctbmod.ERR_ARG
+
+
+def test_device_pointers_in_and_out(ctbmod):
+    torch = pytest.importorskip("torch")
+    xyz, w = synth.thomas(3000, 200.0, 30, 4.0, seed=27, weights="u0.5-1.5")
+    kw = dict(box=200.0, rmin=1.0, rmax=30.0, nbins=4, lmax=5)
+    est = make(ctbmod, **kw)
+    est.set_stream(torch.cuda.current_stream())
+    est.use_torch_allocator()
+    est.set_points(torch.from_numpy(xyz).cuda(), torch.from_numpy(w).cuda())
+    out = torch.zeros(est.zeta_shape, dtype=torch.float64, device="cuda")
+    est.compute(out=out)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert zeta_err(out.cpu().numpy(), ref) < TOL_FP32
+
+
+# ------------------------------------------------------------------ full sizes
+
+
+@pytest.mark.slow
+def test_thomas_1m_sampled_primaries(ctbmod):
+    """1M Thomas points, L = 1000, r in [5, 200], 20 bins, l_max 10: the full
+    launch's zeta is checked by partition; sampled primaries against the oracle."""
+    xyz, w = synth.thomas_1m()
+    kw = synth.config_params(2)
+    est = make(ctbmod, **kw)
+    est.set_points(xyz, w)
+    prim = synth.sample_primaries(xyz.shape[0], 96, seed=7)
+    z = est.compute_subset(prim)
+    ref = oracle.zeta(xyz, w, prim=prim, **kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < TOL_FP32
