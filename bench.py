@@ -250,10 +250,19 @@ def run_ours(args):
     d_w = torch.from_numpy(w).to(dev)
     d_zeta = torch.zeros(est.zeta_shape, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    d_prim = None
+    if args.primaries:
+        # profiling case: the same catalogue and kernels, fewer primaries
+        from paper_2604_08855_gb300 import synth
+        d_prim = torch.from_numpy(synth.sample_primaries(xyz.shape[0], args.primaries, seed=7)).to(dev)
+        cfg = {**cfg, "primaries": args.primaries, "note": "primary subset (profiling case)"}
 
     def step():
         est.set_points(d_xyz, d_w)
-        est.compute(out=d_zeta)
+        if d_prim is None:
+            est.compute(out=d_zeta)
+        else:
+            est.compute_subset(d_prim, out=d_zeta)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -286,7 +295,7 @@ def run_ours(args):
     # end to end through the public API with host buffers
     zh = np.zeros(est.zeta_shape)
     e2e_t = []
-    for k in range(max(2, min(args.steps, 5)) + 1):
+    for k in range(0 if args.no_e2e else max(2, min(args.steps, 5)) + 1):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         est.set_points(xyz, w)
@@ -294,7 +303,7 @@ def run_ours(args):
         dt = time.perf_counter() - t0
         if k > 0:
             e2e_t.append(dt)
-    e2e_s = max_over_ranks(world, float(np.mean(e2e_t)))
+    e2e_s = max_over_ranks(world, float(np.mean(e2e_t)) if e2e_t else float("nan"))
     e2e = {"value": world * updates / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(xyz.nbytes + w.nbytes), "d2h_bytes_per_step": int(zh.nbytes + 8)}
 
@@ -342,6 +351,9 @@ def main():
     ap.add_argument("--workload", default="thomas_1m")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--primaries", type=int, default=0,
+                    help="profiling case: time ctb_compute_subset over this many seeded primaries")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
             os.makedirs(_BUILD, exist_ok=True)
             tmp = _LIB + f".tmp{os.getpid()}"
             cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-                   "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+                   "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB)
     return _LIB

@@ -57,7 +57,7 @@ struct ctb_ctx {
   bool tables_ready = false;
   // device buffers
   Buf xyz_stage, w_stage, key0, val0, key1, val1, hist, scan_tmp, pts_in, pts, s2i, i2s, cell_start;
-  Buf flags, bbox_part, lists, M, wprim, partial, zeta, prim, counters, norm, slot, idx64, alm;
+  Buf flags, bbox_part, lists, M, wprim, partial, zeta, prim, counters, norm, slot, idx64, alm, thr;
   cudaEvent_t ev[2 + 3 * kMaxChunkEvents + 4] = {};
   bool ev_ready = false;
   double t_ms[kStages] = {0, 0, 0, 0, 0, 0};
@@ -132,7 +132,7 @@ void release_all(ctb_ctx* c) {
   Buf* all[] = {&c->xyz_stage, &c->w_stage, &c->key0, &c->val0, &c->key1, &c->val1, &c->hist,
                 &c->scan_tmp, &c->pts_in, &c->pts, &c->s2i, &c->i2s, &c->cell_start, &c->flags,
                 &c->bbox_part, &c->lists, &c->M, &c->wprim, &c->partial, &c->zeta, &c->prim,
-                &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm};
+                &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr};
   for (Buf* b : all) release(c, *b);
   c->tables_ready = false;
 }
@@ -170,6 +170,91 @@ int ensure_tables(ctb_ctx* c) {
   c->tables_ready = true;
   return CTB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// exact bin-edge thresholds: fixed-width unsigned big integers (16 x 32 bits)
+
+struct U512 {
+  uint32_t w[16];
+};
+
+U512 u_from(uint64_t v) {
+  U512 r{};
+  r.w[0] = (uint32_t)v;
+  r.w[1] = (uint32_t)(v >> 32);
+  return r;
+}
+
+U512 u_mul(const U512& a, uint64_t m) {
+  U512 r{};
+  const uint64_t part[2] = {m & 0xffffffffull, m >> 32};
+  for (int h = 0; h < 2; ++h) {
+    uint64_t carry = 0;
+    for (int i = 0; i + h < 16; ++i) {
+      uint64_t t = (uint64_t)a.w[i] * part[h] + r.w[i + h] + carry;
+      r.w[i + h] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+  return r;
+}
+
+U512 u_shl(const U512& a, int k) {
+  U512 r{};
+  const int q = k / 32, s = k % 32;
+  for (int i = 15; i >= 0; --i) {
+    uint64_t v = 0;
+    if (i - q >= 0) v = (uint64_t)a.w[i - q] << s;
+    if (s && i - q - 1 >= 0) v |= (uint64_t)a.w[i - q - 1] >> (32 - s);
+    r.w[i] = (uint32_t)v;
+  }
+  return r;
+}
+
+int u_cmp(const U512& a, const U512& b) {
+  for (int i = 15; i >= 0; --i)
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+  return 0;
+}
+
+void split_double(double d, uint64_t* m, int* e) {
+  int x = 0;
+  double f = std::frexp(d, &x);
+  *m = (uint64_t)std::ldexp(f, 53);
+  *e = x - 53;
+}
+
+}  // namespace
+
+// smallest T >= 0 with T * unit^2 >= edge^2 (edge >= 0, unit > 0), exactly
+unsigned long long ctb::sq_threshold(double edge, double unit) {
+  if (!(edge > 0)) return 0ull;
+  uint64_t mE, mu;
+  int eE, eu;
+  split_double(edge, &mE, &eE);
+  split_double(unit, &mu, &eu);
+  const U512 mu2 = u_mul(u_from(mu), mu);
+  U512 rhs = u_mul(u_from(mE), mE);
+  const int k = 2 * eE - 2 * eu;
+  if (k > 0) rhs = u_shl(rhs, k);
+  auto ok = [&](unsigned long long T) {
+    U512 lhs = u_mul(mu2, T);
+    if (k < 0) lhs = u_shl(lhs, -k);
+    return u_cmp(lhs, rhs) >= 0;
+  };
+  unsigned long long lo = 0, hi = 1ull << 62;
+  if (!ok(hi)) return hi;
+  while (lo < hi) {
+    unsigned long long mid = lo + (hi - lo) / 2;
+    if (ok(mid))
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+namespace {
 
 int bits_for(uint32_t ncells) {
   int b = 0;
@@ -211,7 +296,7 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   g.lmax = c->lmax;
   uint32_t nc = 1;
   if (c->periodic) {
-    c->unit = c->box / 4294967296.0;
+    c->unit = std::ldexp(c->box, -32);
     g.shift = 32;
     double ncd = std::floor(c->box * cpr / c->rmax);
     nc = (uint32_t)std::max(1.0, std::min(ncd, 1024.0));
@@ -242,8 +327,11 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
     double ext = 0;
     for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
     if (!(ext > 0)) ext = c->rmax;
-    // the bounding cube spans at most 2^31 - 1024 units: int32 differences never overflow
-    c->unit = ext / (2147483648.0 - 1024.0);
+    // a power-of-two unit with the bounding cube spanning at most 2^31 - 1024
+    // units: int32 differences never overflow, and a catalogue already on that
+    // dyadic grid is represented exactly
+    c->unit = std::ldexp(1.0, (int)std::ceil(std::log2(ext / (2147483648.0 - 1024.0))));
+    while (ext / c->unit > 2147483648.0 - 1024.0) c->unit *= 2.0;
     for (int k = 0; k < 3; ++k) c->origin[k] = lo[k];
     g.shift = 31;
     double rmax_u = c->rmax / c->unit;
@@ -253,13 +341,29 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   g.nc = nc;
   g.ncells = nc * nc * nc;
   const double rmin_u = c->rmin / c->unit, rmax_u = c->rmax / c->unit;
-  g.rmin2_u = (float)(rmin_u * rmin_u);
-  g.rmax2_u = (float)(rmax_u * rmax_u);
+  g.rlo2_u = (float)(rmin_u * rmin_u * (1.0 - 1e-5));
+  g.rhi2_u = (float)(rmax_u * rmax_u * (1.0 + 1e-5));
   g.rmin_u = (float)rmin_u;
   g.inv_dr_u = (float)(c->nbins / (rmax_u - rmin_u));
   g.cell_scale = (float)(nc / std::ldexp(1.0, g.shift));
   g.rcell = (float)(rmax_u * nc / std::ldexp(1.0, g.shift) * (1.0 + 1e-5) + 1e-3);
   c->g = g;
+
+  // exact edges, the same FP64 values an FP64 evaluation of the bins uses:
+  // r_min, r_min + b (r_max - r_min)/nbins, r_max
+  {
+    std::vector<unsigned long long> thr(c->nbins + 1);
+    const double dr = (c->rmax - c->rmin) / c->nbins;
+    thr[0] = sq_threshold(c->rmin, c->unit);
+    for (int b = 1; b < c->nbins; ++b) {
+      const double bd = b * dr;
+      thr[b] = sq_threshold(c->rmin + bd, c->unit);
+    }
+    thr[c->nbins] = sq_threshold(c->rmax, c->unit);
+    CK(c, ensure(c, c->thr, thr.size() * 8));
+    CK(c, cudaMemcpyAsync(c->thr.p, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
 
   // buffers
   const size_t nn = (size_t)std::max<int64_t>(n, 1);
@@ -345,6 +449,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   a.work = work;
   a.npairs = npairs;
   a.norm = P<float>(c->norm);
+  a.thr = P<unsigned long long>(c->thr);
   a.g = c->g;
   a.row = c->lay.row;
   std::memcpy(a.beta, c->beta, sizeof(a.beta));

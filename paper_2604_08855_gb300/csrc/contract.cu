@@ -13,39 +13,45 @@ constexpr int kConThreads = 512;
 constexpr int kConMaxPer = 24;       // entries per thread (registers)
 constexpr int kConFlush = 64;        // primaries per FP32 partial before FP64
 constexpr int kConSmemFloats = 24576;  // 96 KB of staged rows
-
 constexpr int kConGroup = kConThreads * kConMaxPer;  // entries per block (grid.y splits more)
 
 // Block (x, y) owns partial row (part0 + x), a contiguous range of primaries,
 // and entries [y * kConGroup, (y+1) * kConGroup) of the upper triangle
-// (l, b1 <= b2); each thread owns up to kConMaxPer of them.  FP32 sums over
-// kConFlush primaries, then FP64.
+// (l, b1 <= b2); each thread owns up to kConMaxPer of them.  Staged rows use
+// an odd smem stride (row + 1 floats) so that lanes reading the same slot of
+// different bins hit different banks.  FP32 sums over kConFlush primaries,
+// then FP64.
 __global__ void __launch_bounds__(kConThreads) k_contract_fp32(ContractArgs a) {
   extern __shared__ float s_dyn[];
-  const int nb = a.nbins, row = a.row;
-  const int rowsz = nb * row;
-  const int rows_cap = rowsz > kConSmemFloats ? rowsz : kConSmemFloats;
+  __shared__ int s_slot[(kLmaxCap + 1) * (kLmaxCap + 1)];
+  const int nb = a.nbins, row = a.row, srow = a.row + 1;
+  const int rowsz = nb * row, srowsz = nb * srow;
+  const int rows_cap = srowsz > kConSmemFloats ? srowsz : kConSmemFloats;
   float* s_rows = s_dyn;
-  uint32_t* s_meta = reinterpret_cast<uint32_t*>(s_dyn + rows_cap);
-  int* s_slot = reinterpret_cast<int*>(s_meta + kConGroup);
   const int T = nb * (nb + 1) / 2;
   const int e_lo = blockIdx.y * kConGroup;
   const int E = min((a.lmax + 1) * T - e_lo, kConGroup);
   const int nc = (a.lmax + 1) * (a.lmax + 1);
   for (int c = threadIdx.x; c < nc; c += blockDim.x) s_slot[c] = a.slot[c];
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    int l = (e + e_lo) / T, r = (e + e_lo) % T, b1 = 0;
-    while (r >= nb - b1) {
-      r -= nb - b1;
-      ++b1;
+  uint32_t md[kConMaxPer];
+#pragma unroll
+  for (int k = 0; k < kConMaxPer; ++k) {
+    const int e = threadIdx.x + k * kConThreads;
+    md[k] = 0;
+    if (e < E) {
+      int l = (e + e_lo) / T, r = (e + e_lo) % T, b1 = 0;
+      while (r >= nb - b1) {
+        r -= nb - b1;
+        ++b1;
+      }
+      const int b2 = b1 + r;
+      md[k] = (uint32_t)l | ((uint32_t)b1 << 5) | ((uint32_t)b2 << 11);
     }
-    int b2 = b1 + r;
-    s_meta[e] = (uint32_t)l | ((uint32_t)b1 << 5) | ((uint32_t)b2 << 11);
   }
   const int64_t per = (a.np + gridDim.x - 1) / gridDim.x;
   const int64_t p0 = (int64_t)blockIdx.x * per;
   const int64_t p1 = min(a.np, p0 + per);
-  const int stage = rows_cap / rowsz;
+  const int stage = rows_cap / srowsz;
   float acc[kConMaxPer];
   double acc64[kConMaxPer];
 #pragma unroll
@@ -57,21 +63,23 @@ __global__ void __launch_bounds__(kConThreads) k_contract_fp32(ContractArgs a) {
   __syncthreads();
   for (int64_t pb = p0; pb < p1; pb += stage) {
     const int cnt = (int)min((int64_t)stage, p1 - pb);
-    const float4* src = reinterpret_cast<const float4*>(a.M + (uint64_t)pb * rowsz);
-    float4* dst = reinterpret_cast<float4*>(s_rows);
-    for (int k = threadIdx.x; k < cnt * rowsz / 4; k += blockDim.x) dst[k] = __ldcs(src + k);
+    const float* src = a.M + (uint64_t)pb * rowsz;
+    for (int k = threadIdx.x; k < cnt * rowsz; k += blockDim.x) {
+      const int rr = k / row, cc = k - rr * row;  // rr = primary * nb + bin
+      s_rows[rr * srow + cc] = __ldcs(src + k);
+    }
     __syncthreads();
     for (int q = 0; q < cnt; ++q) {
       const float wp = a.wprim[pb + q];
-      const float* A = s_rows + q * rowsz;
+      const float* A = s_rows + q * srowsz;
 #pragma unroll
       for (int k = 0; k < kConMaxPer; ++k) {
         const int e = threadIdx.x + k * kConThreads;
         if (e < E) {
-          const uint32_t md = s_meta[e];
-          const int l = md & 31, b1 = (md >> 5) & 63, b2 = (md >> 11) & 63;
-          const float* A1 = A + b1 * row;
-          const float* A2 = A + b2 * row;
+          const uint32_t m = md[k];
+          const int l = m & 31, b1 = (m >> 5) & 63, b2 = (m >> 11) & 63;
+          const float* A1 = A + b1 * srow;
+          const float* A2 = A + b2 * srow;
           const int c0 = l * l;
           float s = 0.f;
           for (int c = c0; c <= c0 + 2 * l; ++c) {
@@ -97,8 +105,8 @@ __global__ void __launch_bounds__(kConThreads) k_contract_fp32(ContractArgs a) {
   for (int k = 0; k < kConMaxPer; ++k) {
     const int e = threadIdx.x + k * kConThreads;
     if (e < E) {
-      const uint32_t md = s_meta[e];
-      const int l = md & 31, b1 = (md >> 5) & 63, b2 = (md >> 11) & 63;
+      const uint32_t m = md[k];
+      const int l = m & 31, b1 = (m >> 5) & 63, b2 = (m >> 11) & 63;
       out[((size_t)l * nb + b1) * nb + b2] += acc64[k] + (double)acc[k];
     }
   }
@@ -108,11 +116,10 @@ cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t
   const int E = (a.lmax + 1) * a.nbins * (a.nbins + 1) / 2;
   const int groups = (E + kConGroup - 1) / kConGroup;
   if (a.np == 0) return cudaSuccess;
-  const int rowsz = a.nbins * a.row;
-  const int rows_cap = rowsz > kConSmemFloats ? rowsz : kConSmemFloats;
-  const size_t smem = (size_t)rows_cap * sizeof(float) + (size_t)kConGroup * sizeof(uint32_t) +
-                      (size_t)(kLmaxCap + 1) * (kLmaxCap + 1) * sizeof(int);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const int srowsz = a.nbins * (a.row + 1);
+  const int rows_cap = srowsz > kConSmemFloats ? srowsz : kConSmemFloats;
+  const size_t smem = (size_t)rows_cap * sizeof(float);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_contract_fp32<<<dim3(nparts, groups), kConThreads, smem, st>>>(a);

@@ -34,8 +34,8 @@ struct Geom {
   uint32_t ncells;     // nc^3
   int nbins;
   int lmax;            // requested ell_max
-  float rmin2_u;       // r_min^2 in units^2
-  float rmax2_u;       // r_max^2 in units^2
+  float rlo2_u;        // r_min^2 in units^2, widened by 1e-5 (float pre-filter)
+  float rhi2_u;        // r_max^2 in units^2, widened by 1e-5 (float pre-filter)
   float rmin_u;        // r_min in units
   float inv_dr_u;      // nbins / (r_max - r_min) in 1/units
   float rcell;         // r_max in cell units, padded by a small slack
@@ -110,6 +110,11 @@ void make_layout(int L, Layout* out);
 // kernels launched by this host thread (every launcher adds its launches)
 extern thread_local unsigned long long g_launches;
 
+// smallest integer T >= 0 with T * unit^2 >= edge^2, in exact arithmetic
+// (api.cu); a pair whose squared separation in units^2 is T lies at or
+// beyond `edge` exactly when T >= threshold.
+unsigned long long sq_threshold(double edge, double unit);
+
 // recurrence constants (pair_dispatch.cu)
 void fill_beta(float* beta);   // beta_lm at [l*(kLmaxCap+1)+m]
 double norm_lm(int l, int m);  // C_lm of the real orthonormal Y_l,m
@@ -164,6 +169,7 @@ struct PairArgs {
   unsigned long long* work;   // work counter (zeroed before launch)
   unsigned long long* npairs; // binned-pair counter (accumulated)
   const float* norm;          // [row] normalisation per slot
+  const unsigned long long* thr; // [nbins+1] exact bin edges: r^2 (units^2) >= thr[b]  <=>  r >= edge b
   Geom g;
   int row;                    // floats per (primary, bin) row
   float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];  // recurrence beta_lm at [l*(kLmaxCap+1)+m]

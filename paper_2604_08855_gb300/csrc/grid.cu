@@ -14,7 +14,7 @@ namespace ctb {
 // ingest: float64 xyz / w  ->  fixed-point uint4 point, cell key, index
 
 __global__ void k_ingest(const double* __restrict__ xyz, const double* __restrict__ w, int64_t n,
-                         double inv_box, double ox, double oy, double oz, double inv_unit, Geom g,
+                         double box, double ox, double oy, double oz, double inv_unit, Geom g,
                          uint32_t* __restrict__ key, uint32_t* __restrict__ val, uint4* __restrict__ pts,
                          uint32_t* flags) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -33,8 +33,9 @@ __global__ void k_ingest(const double* __restrict__ xyz, const double* __restric
     for (int k = 0; k < 3; ++k) {
       double s;
       if (g.periodic) {
-        double t = p[k] * inv_box;
-        t -= floor(t);                       // wrap into [0, 1)
+        double t = p[k] / box;               // correctly rounded: a point on the
+        t -= floor(t);                       // L/2^32 grid maps to its exact unit
+        if (t >= 1.0) t = 0.0;
         s = t * 4294967296.0;                // 2^32 units per side
         if (!(s < 4294967295.0)) s = 4294967295.0;
       } else {
@@ -57,10 +58,9 @@ cudaError_t launch_ingest(const double* xyz, const double* w, int64_t n, double 
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 65535 * 4) blocks = 65535 * 4;
-  double inv_box = box > 0 ? 1.0 / box : 0.0;
   double o[3] = {0, 0, 0};
   if (origin3) { o[0] = origin3[0]; o[1] = origin3[1]; o[2] = origin3[2]; }
-  k_ingest<<<blocks, 256, 0, st>>>(xyz, w, n, inv_box, o[0], o[1], o[2], inv_unit, g, out.key,
+  k_ingest<<<blocks, 256, 0, st>>>(xyz, w, n, box, o[0], o[1], o[2], inv_unit, g, out.key,
                                    out.val, out.pts, d_flags);
   ++g_launches;
   return cudaGetLastError();

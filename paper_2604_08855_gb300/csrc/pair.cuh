@@ -362,12 +362,26 @@ __global__ void __launch_bounds__(128, 3) k_pair(PairArgs a) {
           const float dy = __int2float_rn((int)(q.y - P.y));
           const float dz = __int2float_rn((int)(q.z - P.z));
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const bool inb = valid && r2 >= g.rmin2_u && r2 < g.rmax2_u && r2 > 0.f;
+          bool inb = valid && r2 > 0.f && r2 >= g.rlo2_u && r2 < g.rhi2_u;
           int b = 0;
           if (inb) {
             const float r = r2 * rsqrtf(r2);
-            b = (int)((r - g.rmin_u) * g.inv_dr_u);
-            b = min(max(b, 0), nbins - 1);
+            const float t = (r - g.rmin_u) * g.inv_dr_u;
+            b = (int)floorf(t);
+            const float fr = t - (float)b;
+            if (b < 0 || b >= nbins || fr < 1e-4f || fr > 1.f - 1e-4f) {
+              // within float rounding of an edge: decide on the exact squared
+              // separation (integer units^2) against the exact thresholds
+              const long long ix = (int)(q.x - P.x), iy = (int)(q.y - P.y), iz = (int)(q.z - P.z);
+              const unsigned long long e2 = (unsigned long long)(ix * ix + iy * iy + iz * iz);
+              if (e2 == 0ull || e2 < __ldg(a.thr) || e2 >= __ldg(a.thr + nbins)) {
+                inb = false;
+              } else {
+                b = min(max(b, 0), nbins - 1);
+                while (e2 < __ldg(a.thr + b)) --b;
+                while (e2 >= __ldg(a.thr + b + 1)) ++b;
+              }
+            }
           }
           const unsigned act = __ballot_sync(0xffffffffu, inb);
           bool full = false;

@@ -21,12 +21,35 @@ from __future__ import annotations
 import numpy as np
 
 # ---------------------------------------------------------------------------
+# fixed-point grids
+#
+# Every generated coordinate is snapped onto a fine grid: the L / 2^32 grid of
+# a periodic cube (L = 1000 and 2000 have short mantissas, so grid points are
+# exact float64 values and x / L * 2^32 is an exact integer), or a dyadic grid
+# for open space.  A bin decision then depends only on an exact squared
+# separation, identical for every exact evaluation; the statistics are
+# unchanged (the grid step is ~1e-7 of the box).
+
+
+def snap_periodic(xyz, box: float):
+    """Wrap into [0, box) and snap onto the box / 2^32 grid (exact for box = 1000, 2000)."""
+    k = np.floor(np.mod(np.asarray(xyz, dtype=np.float64), box) / box * 4294967296.0)
+    k = np.clip(k, 0.0, 4294967295.0)
+    return k * (box / 4294967296.0)
+
+
+def snap_dyadic(xyz, step: float = 2.0 ** -20):
+    """Snap onto the grid of multiples of a power of two (open space)."""
+    return np.round(np.asarray(xyz, dtype=np.float64) / step) * step
+
+
+# ---------------------------------------------------------------------------
 # primitive generators
 
 
 def uniform(n: int, box: float, seed: int, weights: str = "unit"):
     rng = np.random.default_rng(seed)
-    xyz = rng.uniform(0.0, box, size=(n, 3))
+    xyz = snap_periodic(rng.uniform(0.0, box, size=(n, 3)), box)
     w = _weights(rng, n, weights)
     return xyz, w
 
@@ -37,8 +60,7 @@ def thomas(n: int, box: float, n_par: int, sigma: float, seed: int, weights: str
     parents = rng.uniform(0.0, box, size=(n_par, 3))
     owner = rng.integers(0, n_par, size=n)
     xyz = parents[owner] + rng.normal(0.0, sigma, size=(n, 3))
-    xyz = np.mod(xyz, box)
-    xyz[xyz >= box] = 0.0  # np.mod can round up to box itself
+    xyz = snap_periodic(xyz, box)
     w = _weights(rng, n, weights)
     return xyz, w
 
@@ -75,7 +97,7 @@ def sector_randoms(n: int, seed: int):
     r3 = rng.uniform(SECTOR_R[0] ** 3, SECTOR_R[1] ** 3, size=n)
     r = np.cbrt(r3)
     cdec = np.sqrt(1.0 - sdec * sdec)
-    return np.stack([r * cdec * np.cos(ra), r * cdec * np.sin(ra), r * sdec], axis=1)
+    return snap_dyadic(np.stack([r * cdec * np.cos(ra), r * cdec * np.sin(ra), r * sdec], axis=1))
 
 
 def sector_data(n: int, seed: int, sigma: float = 5.0, per_parent: float = 100.0):
@@ -100,7 +122,7 @@ def sector_data(n: int, seed: int, sigma: float = 5.0, per_parent: float = 100.0
             break
         total = int(total * 1.2)
     pick = rng.choice(xyz.shape[0], size=n, replace=False)
-    return xyz[np.sort(pick)]
+    return snap_dyadic(xyz[np.sort(pick)])
 
 
 # ---------------------------------------------------------------------------

@@ -46,6 +46,8 @@ def run_full(ctbmod, xyz, w, kw, **opts):
 @pytest.mark.parametrize("lmax", [0, 3, 10])
 def test_small_thomas_vs_oracle(ctbmod, box, lmax):
     xyz, w = synth.thomas(4000, 400.0, 40, 5.0, seed=21, weights="u0.5-1.5")
+    if box == 0.0:
+        xyz = synth.snap_dyadic(xyz, 2.0 ** -16)
     kw = dict(box=box, rmin=2.0, rmax=60.0, nbins=7, lmax=lmax)
     z, est = run_full(ctbmod, xyz, w, kw)
     ref = oracle.zeta(xyz, w, **kw)
@@ -130,7 +132,7 @@ def test_edge_hand_triangle_and_faces(ctbmod):
     from numpy.polynomial import legendre as npleg
     t = np.deg2rad(120.0)
     O = np.array([0.2, 99.9, 50.0])
-    pts = np.array([O, O + [15.0, 0, 0], O + [25 * np.cos(t), 25 * np.sin(t), 0]]) % 100.0
+    pts = synth.snap_periodic(np.array([O, O + [15.0, 0, 0], O + [25 * np.cos(t), 25 * np.sin(t), 0]]), 100.0)
     w = np.array([1.3, 0.7, -0.4])
     kw = dict(box=100.0, rmin=10.0, rmax=30.0, nbins=2, lmax=10)
     z, _ = run_full(ctbmod, pts, w, kw)
@@ -142,7 +144,7 @@ def test_edge_hand_triangle_and_faces(ctbmod):
 
 def test_edge_all_in_one_cell_nbins1_rmin0(ctbmod):
     rng = np.random.default_rng(3)
-    xyz = 50.0 + rng.uniform(-1, 1, size=(300, 3))
+    xyz = synth.snap_dyadic(50.0 + rng.uniform(-1, 1, size=(300, 3)), 2.0 ** -20)
     w = rng.uniform(0.5, 1.5, 300)
     kw = dict(box=0.0, rmin=0.0, rmax=4.0, nbins=1, lmax=6)
     z, _ = run_full(ctbmod, xyz, w, kw)
@@ -153,7 +155,7 @@ def test_edge_all_in_one_cell_nbins1_rmin0(ctbmod):
 def test_edge_coincident_points_and_small_box(ctbmod):
     """Duplicated points (r = 0 never binned) in a box only a few cells wide."""
     rng = np.random.default_rng(4)
-    base = rng.uniform(0, 10.0, size=(200, 3))
+    base = synth.snap_periodic(rng.uniform(0, 10.0, size=(200, 3)), 10.0)
     xyz = np.concatenate([base, base[:50]])
     w = rng.uniform(0.5, 1.5, xyz.shape[0])
     kw = dict(box=10.0, rmin=0.0, rmax=5.0, nbins=3, lmax=5)
@@ -163,12 +165,12 @@ def test_edge_coincident_points_and_small_box(ctbmod):
 
 
 def test_edge_negative_weights_and_wrap_inputs(ctbmod):
-    xyz, _ = synth.uniform(3000, 200.0, seed=9)
-    xyz = xyz + np.array([-200.0, 400.0, -600.0])  # periodic images of the same catalogue
+    xyz, _ = synth.uniform(3000, 250.0, seed=9)
+    xyz = xyz + np.array([-250.0, 500.0, -750.0])  # periodic images of the same catalogue
     w = np.random.default_rng(9).uniform(-1.0, 1.0, xyz.shape[0])
-    kw = dict(box=200.0, rmin=2.0, rmax=30.0, nbins=5, lmax=8)
+    kw = dict(box=250.0, rmin=2.0, rmax=30.0, nbins=5, lmax=8)
     z, _ = run_full(ctbmod, xyz, w, kw)
-    ref = oracle.zeta(np.mod(xyz, 200.0), w, **kw)
+    ref = oracle.zeta(np.mod(xyz, 250.0), w, **kw)
     # negative primary weights: the Gram bound still scales every entry
     assert zeta_err(z, ref) < TOL_FP32
 

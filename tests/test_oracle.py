@@ -314,3 +314,15 @@ def test_ambiguous_pair_count():
     assert r["namb"] == 2 and r["npairs"] == 2
     # half-open bins: r = 20 belongs to bin 1
     assert r["wpairs"][1] == 2.0 and r["wpairs"][0] == 0.0
+
+
+def test_generators_are_on_the_fixed_point_grid():
+    """Snapped catalogues: x / L * 2^32 is an exact integer (periodic), and
+    x * 2^20 an exact integer (open space)."""
+    for box in (1000.0, 2000.0, 400.0, 250.0):
+        xyz, _ = synth.thomas(5000, box, 50, 5.0, seed=1)
+        k = xyz / box * 4294967296.0
+        assert np.all(k == np.floor(k)) and np.all(k >= 0) and np.all(k < 4294967296.0)
+    s = synth.sector_randoms(5000, seed=6)
+    assert np.all(s * 2.0 ** 20 == np.floor(s * 2.0 ** 20))
+    assert np.all(synth.in_sector(s))
