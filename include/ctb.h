@@ -169,9 +169,10 @@ int ctb_set_allocator(ctb_ctx* ctx, void* (*alloc)(size_t bytes, void* user),
 /*
  * Per-stage device times of the last ctb_set_points / ctb_compute* call, in
  * milliseconds, measured with CUDA events on the context's stream:
- *   [0] ingest  [1] sort + grid  [2] pair multipoles  [3] pack
+ *   [0] ingest  [1] sort + grid  [2] pair multipoles (= [6] + [7])  [3] pack
  *   [4] contraction  [5] reduce + normalise
- * Writes min(cap, 6) values; returns the number written.
+ *   [6] neighbour enumeration (count + scan + fill)  [7] harmonic accumulation
+ * Writes min(cap, 8) values; returns the number written.
  */
 int ctb_get_timings(ctb_ctx* ctx, double* ms_per_stage, int cap);
 

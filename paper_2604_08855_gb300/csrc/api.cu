@@ -23,8 +23,7 @@ struct Buf {
 
 thread_local std::string g_create_err;
 
-constexpr int kStages = 6;
-constexpr int kMaxChunkEvents = 256;
+constexpr int kStages = 8;
 
 }  // namespace
 
@@ -51,6 +50,7 @@ struct ctb_ctx {
   Geom g{};
   double unit = 0;
   double origin[3] = {0, 0, 0};
+  double bbox_volume = 0;
   Layout lay{};
   int Lk = 0;
   float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];
@@ -58,9 +58,11 @@ struct ctb_ctx {
   // device buffers
   Buf xyz_stage, w_stage, key0, val0, key1, val1, hist, scan_tmp, pts_in, pts, s2i, i2s, cell_start;
   Buf flags, bbox_part, lists, M, wprim, partial, zeta, prim, counters, norm, slot, idx64, alm, thr;
-  cudaEvent_t ev[2 + 3 * kMaxChunkEvents + 4] = {};
+  Buf counts, offsets, scan_tmp2;
+  uint64_t list_cap = (uint64_t)1 << 32;  // neighbour-list entries per chunk (16 GB)
+  cudaEvent_t ev[16] = {};
   bool ev_ready = false;
-  double t_ms[kStages] = {0, 0, 0, 0, 0, 0};
+  double t_ms[kStages] = {0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t npairs = 0;
   unsigned long long launches_points = 0, launches_compute = 0;
 };
@@ -132,7 +134,8 @@ void release_all(ctb_ctx* c) {
   Buf* all[] = {&c->xyz_stage, &c->w_stage, &c->key0, &c->val0, &c->key1, &c->val1, &c->hist,
                 &c->scan_tmp, &c->pts_in, &c->pts, &c->s2i, &c->i2s, &c->cell_start, &c->flags,
                 &c->bbox_part, &c->lists, &c->M, &c->wprim, &c->partial, &c->zeta, &c->prim,
-                &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr};
+                &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr, &c->counts,
+                &c->offsets, &c->scan_tmp2};
   for (Buf* b : all) release(c, *b);
   c->tables_ready = false;
 }
@@ -325,7 +328,11 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
         }
     }
     double ext = 0;
-    for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
+    c->bbox_volume = 1.0;
+    for (int k = 0; k < 3; ++k) {
+      ext = std::max(ext, hi[k] - lo[k]);
+      c->bbox_volume *= std::max(hi[k] - lo[k], c->rmax);
+    }
     if (!(ext > 0)) ext = c->rmax;
     // a power-of-two unit with the bounding cube spanning at most 2^31 - 1024
     // units: int32 differences never overflow, and a catalogue already on that
@@ -399,76 +406,144 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   if (fl) return fail(c, CTB_ERR_NONFINITE, "non-finite coordinate or weight");
+  for (int k = 0; k < kStages; ++k) c->t_ms[k] = 0;
   c->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
   c->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
-  for (int k = 2; k < kStages; ++k) c->t_ms[k] = 0;
   c->n = n;
   return CTB_OK;
 }
 
 // ---------------------------------------------------------------------------
-// pair kernel + contraction over a primary list (prim == NULL: all points)
+// pair multipoles + contraction over a primary list (prim == NULL: all points)
+//
+// Per chunk of primaries: count pairs per (primary, bin) -> read the chunk's
+// total (one small device->host copy) -> exclusive scan -> fill the
+// (primary, bin) neighbour lists -> accumulate a_lm per list -> contract.
+// A chunk whose lists would not fit the list buffer is halved and recounted;
+// the next chunk's size follows the observed pairs per primary.
 
 struct PairPlan {
-  int wpb, nblocks;
-  int64_t chunk;
+  int wpb, alm_blocks, stream_blocks, count_blocks;
+  int64_t chunk_first;   // primaries in the first chunk (from the mean density)
+  int64_t chunk_max;     // primaries per chunk at most
+  uint64_t list_cap;     // neighbour-list entries per chunk at most
   int nparts;
 };
 
 int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   int wpb = c->wpb > 0 ? c->wpb : 4;
-  int bps = pair_max_blocks_per_sm(c->Lk, wpb);
-  if (bps < 1) return fail(c, CTB_ERR_CUDA, "pair kernel cannot be resident with this block size");
+  int bps = alm_blocks_per_sm(c->Lk, wpb);
+  int sbps = stream_blocks_per_sm(true, c->nbins);
+  int cbps = stream_blocks_per_sm(false, c->nbins);
+  if (bps < 1 || sbps < 1 || cbps < 1) return fail(c, CTB_ERR_CUDA, "pair kernels cannot be resident");
   pl->wpb = wpb;
-  pl->nblocks = bps * c->nsm;
+  pl->alm_blocks = bps * c->nsm;
+  pl->stream_blocks = sbps * c->nsm;
+  pl->count_blocks = cbps * c->nsm;
   const size_t rowbytes = (size_t)c->nbins * c->lay.row * sizeof(float);
-  int64_t chunk = c->chunk > 0 ? c->chunk : (int64_t)((size_t)12 << 30) / (int64_t)rowbytes;
-  chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, std::max<int64_t>(np, 1)));
-  pl->chunk = chunk;
+  int64_t chunk = c->chunk > 0 ? c->chunk : (int64_t)(((size_t)3 << 30) / rowbytes);
+  pl->chunk_max = std::max<int64_t>(1, std::min<int64_t>(chunk, std::max<int64_t>(np, 1)));
+  pl->list_cap = c->list_cap;
   pl->nparts = 2 * c->nsm;
+  // first chunk from the mean density, with a margin for clustering; later
+  // chunks follow the measured pairs per primary
+  const double vol = c->periodic ? c->box * c->box * c->box : c->bbox_volume;
+  const double ball = 4.0 / 3.0 * M_PI * (c->rmax * c->rmax * c->rmax - c->rmin * c->rmin * c->rmin);
+  const double est = vol > 0 ? 2.0 * (double)c->n * std::min(1.0, ball / vol) + 64.0 : 64.0;
+  pl->chunk_first = std::max<int64_t>(1, std::min<int64_t>(pl->chunk_max, (int64_t)(0.9 * (double)pl->list_cap / est)));
   return CTB_OK;
 }
 
-int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, const PairPlan& pl, int* nchunks) {
-  const size_t listwords = (size_t)pl.nblocks * pl.wpb * c->nbins * c->cap;
-  CK(c, ensure(c, c->lists, listwords * 4));
-  CK(c, ensure(c, c->M, (size_t)pl.chunk * c->nbins * c->lay.row * sizeof(float)));
-  CK(c, ensure(c, c->wprim, (size_t)pl.chunk * sizeof(float)));
+// M rows (slot layout) -> [m][nbins][(lmax+1)^2] in the l*l+l+m order
+__global__ void k_unpack_alm(const float* __restrict__ M, int64_t m, int nbins, int row, const int* __restrict__ slot,
+                             int nc, float* __restrict__ out) {
+  const int64_t total = m * nbins * nc;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(o % nc);
+    const int64_t pb = o / nc;
+    out[o] = M[pb * row + slot[c]];
+  }
+}
+
+struct ChunkEv {
+  cudaEvent_t e[6];
+};
+
+int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, const PairPlan& pl,
+              float* alm_dev_out, uint64_t* npairs_out) {
+  const int nb = c->nbins;
+  CK(c, ensure(c, c->counts, (size_t)pl.chunk_max * nb * 4));
+  CK(c, ensure(c, c->offsets, (size_t)pl.chunk_max * nb * 4));
+  CK(c, ensure(c, c->scan_tmp2, scan_tmp_words((size_t)pl.chunk_max * nb) * 4));
+  CK(c, ensure(c, c->M, (size_t)pl.chunk_max * nb * c->lay.row * sizeof(float)));
+  CK(c, ensure(c, c->wprim, (size_t)pl.chunk_max * sizeof(float)));
   CK(c, ensure(c, c->counters, 64));
-  CK(c, cudaMemsetAsync(c->counters.p, 0, 64, c->st));
   unsigned long long* work = P<unsigned long long>(c->counters);
-  unsigned long long* npairs = work + 1;
-  PairArgs a{};
-  a.pts = P<uint4>(c->pts);
-  a.cell_start = P<uint32_t>(c->cell_start);
-  a.prim = dprim;
-  a.M = P<float>(c->M);
-  a.wprim = P<float>(c->wprim);
-  a.lists = P<uint32_t>(c->lists);
-  a.cap = c->cap;
-  a.work = work;
-  a.npairs = npairs;
-  a.norm = P<float>(c->norm);
-  a.thr = P<unsigned long long>(c->thr);
-  a.g = c->g;
-  a.row = c->lay.row;
-  std::memcpy(a.beta, c->beta, sizeof(a.beta));
-  int k = 0;
-  for (int64_t c0 = 0; c0 < np; c0 += pl.chunk, ++k) {
-    const int64_t cnt = std::min(pl.chunk, np - c0);
-    const int evk = std::min(k, kMaxChunkEvents - 1);
-    if (k > 0) CK(c, cudaMemsetAsync(work, 0, sizeof(unsigned long long), c->st));
-    a.prim_begin = c0;
-    a.prim_count = cnt;
-    CK(c, cudaEventRecord(c->ev[2 + 3 * evk], c->st));
-    CK(c, launch_pair(a, c->Lk, pl.wpb, pl.nblocks, c->st));
-    CK(c, cudaEventRecord(c->ev[3 + 3 * evk], c->st));
+  unsigned long long* total = work + 1;
+  StreamArgs sa{};
+  sa.pts = P<uint4>(c->pts);
+  sa.cell_start = P<uint32_t>(c->cell_start);
+  sa.prim = dprim;
+  sa.thr = P<unsigned long long>(c->thr);
+  sa.counts = P<uint32_t>(c->counts);
+  sa.offsets = P<uint32_t>(c->offsets);
+  sa.wprim = P<float>(c->wprim);
+  sa.work = work;
+  sa.total = total;
+  sa.g = c->g;
+  AlmArgs aa{};
+  aa.pts = P<uint4>(c->pts);
+  aa.prim = dprim;
+  aa.counts = P<uint32_t>(c->counts);
+  aa.offsets = P<uint32_t>(c->offsets);
+  aa.M = P<float>(c->M);
+  aa.norm = P<float>(c->norm);
+  aa.work = work;
+  aa.nbins = nb;
+  aa.row = c->lay.row;
+  std::memcpy(aa.beta, c->beta, sizeof(aa.beta));
+  double t_stream = 0, t_alm = 0, t_con = 0;
+  uint64_t pairs = 0;
+  int64_t C = pl.chunk_first;
+  int64_t c0 = 0;
+  cudaEvent_t* ev = c->ev + 2;  // [0] count start [1] count end [2] fill end [3] alm end [4] contract end
+  while (c0 < np) {
+    const int64_t cnt = std::min(C, np - c0);
+    sa.prim_begin = aa.prim_begin = c0;
+    sa.prim_count = aa.prim_count = cnt;
+    CK(c, cudaMemsetAsync(work, 0, 16, c->st));
+    CK(c, cudaEventRecord(ev[0], c->st));
+    sa.lists = nullptr;
+    CK(c, launch_stream(sa, false, pl.count_blocks, c->st));
+    CK(c, cudaEventRecord(ev[1], c->st));
+    unsigned long long tot = 0;
+    CK(c, cudaMemcpyAsync(&tot, total, sizeof(tot), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    t_stream += elapsed(ev[0], ev[1]);
+    if (tot > pl.list_cap) {
+      if (cnt > 1) {
+        C = std::max<int64_t>(1, cnt / 2);
+        continue;
+      }
+      return fail(c, CTB_ERR_OOM, "one primary has more neighbours than the list buffer holds");
+    }
+    CK(c, ensure(c, c->lists, std::max<size_t>((size_t)tot, 1) * 4));
+    CK(c, exclusive_scan_u32(P<uint32_t>(c->counts), P<uint32_t>(c->offsets), (size_t)cnt * nb,
+                             P<uint32_t>(c->scan_tmp2), c->st));
+    sa.lists = P<uint32_t>(c->lists);
+    aa.lists = P<uint32_t>(c->lists);
+    CK(c, cudaMemsetAsync(work, 0, 8, c->st));
+    CK(c, launch_stream(sa, true, pl.stream_blocks, c->st));
+    CK(c, cudaEventRecord(ev[2], c->st));
+    CK(c, cudaMemsetAsync(work, 0, 8, c->st));
+    CK(c, launch_alm(aa, c->Lk, pl.wpb, pl.alm_blocks, c->st));
+    CK(c, cudaEventRecord(ev[3], c->st));
     if (contract) {
       ContractArgs ca{};
       ca.M = P<float>(c->M);
       ca.wprim = P<float>(c->wprim);
       ca.np = cnt;
-      ca.nbins = c->nbins;
+      ca.nbins = nb;
       ca.lmax = c->lmax;
       ca.row = c->lay.row;
       ca.slot = P<int>(c->slot);
@@ -476,9 +551,32 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
       ca.part0 = 0;
       CK(c, launch_contract_fp32(ca, pl.nparts, c->st));
     }
-    CK(c, cudaEventRecord(c->ev[4 + 3 * evk], c->st));
+    if (alm_dev_out) {
+      const int ncf = (c->lmax + 1) * (c->lmax + 1);
+      const size_t outsz = (size_t)cnt * nb * ncf;
+      int blocks = (int)std::min<size_t>((outsz + 255) / 256, 65535);
+      k_unpack_alm<<<blocks, 256, 0, c->st>>>(P<float>(c->M), cnt, nb, c->lay.row, P<int>(c->slot), ncf,
+                                              alm_dev_out + (size_t)c0 * nb * ncf);
+      ++g_launches;
+      CK(c, cudaGetLastError());
+    }
+    CK(c, cudaEventRecord(ev[4], c->st));
+    CK(c, cudaEventSynchronize(ev[4]));
+    t_stream += elapsed(ev[1], ev[2]);
+    t_alm += elapsed(ev[2], ev[3]);
+    t_con += elapsed(ev[3], ev[4]);
+    pairs += tot;
+    c0 += cnt;
+    // next chunk: fill about 90 % of the list buffer at the observed density
+    const double per = cnt > 0 ? (double)tot / (double)cnt : 0.0;
+    int64_t nxt = per > 0 ? (int64_t)(0.9 * (double)pl.list_cap / per) : pl.chunk_max;
+    C = std::max<int64_t>(1, std::min<int64_t>(nxt, pl.chunk_max));
   }
-  *nchunks = k;
+  c->t_ms[2] = t_stream + t_alm;
+  c->t_ms[4] = t_con;
+  c->t_ms[6] = t_stream;
+  c->t_ms[7] = t_alm;
+  *npairs_out = pairs;
   return CTB_OK;
 }
 
@@ -496,32 +594,20 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
   CK(c, ensure(c, c->partial, (size_t)pl.nparts * zsz * sizeof(double)));
   CK(c, ensure(c, c->zeta, zsz * sizeof(double)));
   CK(c, cudaMemsetAsync(c->partial.p, 0, (size_t)pl.nparts * zsz * sizeof(double), c->st));
-  int nchunks = 0;
-  const int evs = 2 + 3 * kMaxChunkEvents;
-  CK(c, cudaEventRecord(c->ev[evs], c->st));
-  r = run_pairs(c, dprim, np, true, pl, &nchunks);
+  for (int k = 0; k < kStages; ++k) c->t_ms[k] = 0;
+  uint64_t pairs = 0;
+  r = run_pairs(c, dprim, np, true, pl, nullptr, &pairs);
   if (r) return r;
-  CK(c, cudaEventRecord(c->ev[evs + 1], c->st));
+  const int evs = 2 + 8;
+  CK(c, cudaEventRecord(c->ev[evs], c->st));
   CK(c, launch_finalize(P<double>(c->partial), pl.nparts, c->lmax, c->nbins, P<double>(c->zeta), c->st));
-  CK(c, cudaEventRecord(c->ev[evs + 2], c->st));
+  CK(c, cudaEventRecord(c->ev[evs + 1], c->st));
   const bool dev_out = is_device_ptr(zeta_out);
   CK(c, cudaMemcpyAsync(zeta_out, c->zeta.p, zsz * sizeof(double),
                         dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
-  unsigned long long np_pairs = 0;
-  CK(c, cudaMemcpyAsync(&np_pairs, P<unsigned long long>(c->counters) + 1, sizeof(np_pairs),
-                        cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  c->npairs = np_pairs;
-  double tp = 0, tc = 0;
-  for (int k = 0; k < std::min(nchunks, kMaxChunkEvents); ++k) {
-    tp += elapsed(c->ev[2 + 3 * k], c->ev[3 + 3 * k]);
-    tc += elapsed(c->ev[3 + 3 * k], c->ev[4 + 3 * k]);
-  }
-  c->t_ms[0] = c->t_ms[1] = 0;
-  c->t_ms[2] = tp;
-  c->t_ms[3] = 0;
-  c->t_ms[4] = tc;
-  c->t_ms[5] = elapsed(c->ev[evs + 1], c->ev[evs + 2]);
+  c->npairs = pairs;
+  c->t_ms[5] = elapsed(c->ev[evs], c->ev[evs + 1]);
   return CTB_OK;
 }
 
@@ -563,17 +649,6 @@ int map_primaries(ctb_ctx* c, const int64_t* idx, int64_t m) {
   CK(c, cudaStreamSynchronize(c->st));
   if (fl & 2u) return fail(c, CTB_ERR_ARG, "primary index out of range");
   return CTB_OK;
-}
-
-// M rows (slot layout) -> [m][nbins][(lmax+1)^2] in the l*l+l+m order
-__global__ void k_unpack_alm(const float* __restrict__ M, int64_t m, int nbins, int row, const int* __restrict__ slot,
-                             int nc, float* __restrict__ out) {
-  const int64_t total = m * nbins * nc;
-  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(o % nc);
-    const int64_t pb = o / nc;
-    out[o] = M[pb * row + slot[c]];
-  }
 }
 
 }  // namespace
@@ -676,10 +751,6 @@ int ctb_get_alm(ctb_ctx* c, const int64_t* primary_idx, int64_t m, float* alm_ou
   PairPlan pl{};
   r = plan_pairs(c, m, &pl);
   if (r) return r;
-  pl.chunk = m;
-  int nch = 0;
-  r = run_pairs(c, P<uint32_t>(c->prim), m, false, pl, &nch);
-  if (r) return r;
   const int nc = (c->lmax + 1) * (c->lmax + 1);
   const size_t outsz = (size_t)m * c->nbins * nc;
   const bool dev_out = is_device_ptr(alm_out);
@@ -688,16 +759,12 @@ int ctb_get_alm(ctb_ctx* c, const int64_t* primary_idx, int64_t m, float* alm_ou
     CK(c, ensure(c, c->alm, outsz * 4));
     dst = P<float>(c->alm);
   }
-  int blocks = (int)std::min<size_t>((outsz + 255) / 256, 65535);
-  k_unpack_alm<<<blocks, 256, 0, c->st>>>(P<float>(c->M), m, c->nbins, c->lay.row, P<int>(c->slot), nc, dst);
-  ++g_launches;
-  CK(c, cudaGetLastError());
+  uint64_t pairs = 0;
+  r = run_pairs(c, P<uint32_t>(c->prim), m, false, pl, dst, &pairs);
+  if (r) return r;
   if (!dev_out) CK(c, cudaMemcpyAsync(alm_out, dst, outsz * 4, cudaMemcpyDeviceToHost, c->st));
-  unsigned long long np_pairs = 0;
-  CK(c, cudaMemcpyAsync(&np_pairs, P<unsigned long long>(c->counters) + 1, sizeof(np_pairs),
-                        cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  c->npairs = np_pairs;
+  c->npairs = pairs;
   return CTB_OK;
 }
 

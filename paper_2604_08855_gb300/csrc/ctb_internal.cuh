@@ -155,28 +155,44 @@ cudaError_t launch_gather(const uint32_t* val_sorted, const uint4* pts_in, int64
 cudaError_t launch_cell_start(const uint32_t* key_sorted, int64_t n, uint32_t ncells,
                               uint32_t* cell_start, cudaStream_t st);
 
-// pair.cu
-struct PairArgs {
-  const uint4* pts;           // sorted points
-  const uint32_t* cell_start; // [ncells + 1]
-  const uint32_t* prim;       // sorted positions of the primaries (NULL: identity)
-  int64_t prim_begin;         // first primary of this launch (index into prim / positions)
-  int64_t prim_count;         // primaries in this launch
-  float* M;                   // [prim_count][nbins][row] coefficient rows
-  float* wprim;               // [prim_count] primary weights
-  uint32_t* lists;            // per-warp neighbour lists [warps][nbins][cap]
-  uint32_t cap;               // list capacity per bin (multiple of 4, >= 64)
-  unsigned long long* work;   // work counter (zeroed before launch)
-  unsigned long long* npairs; // binned-pair counter (accumulated)
-  const float* norm;          // [row] normalisation per slot
-  const unsigned long long* thr; // [nbins+1] exact bin edges: r^2 (units^2) >= thr[b]  <=>  r >= edge b
+// stream.cu -- neighbour enumeration (count pass, then fill pass)
+struct StreamArgs {
+  const uint4* pts;               // sorted points
+  const uint32_t* cell_start;     // [ncells + 1]
+  const uint32_t* prim;           // sorted positions of the primaries (NULL: identity)
+  int64_t prim_begin;             // first primary of this launch
+  int64_t prim_count;             // primaries in this launch
+  const unsigned long long* thr;  // [nbins+1] exact edges in units^2
+  uint32_t* counts;               // [prim_count][nbins] pairs per (primary, bin)   (count pass)
+  const uint32_t* offsets;        // [prim_count][nbins] list start per (primary, bin) (fill pass)
+  uint32_t* lists;                // neighbour indices grouped by (primary, bin)      (fill pass)
+  float* wprim;                   // [prim_count] primary weights                      (count pass)
+  unsigned long long* work;       // work counter (zeroed before launch)
+  unsigned long long* total;      // binned pairs of this launch (count pass, accumulated)
   Geom g;
-  int row;                    // floats per (primary, bin) row
+};
+int stream_blocks_per_sm(bool fill, int nbins);
+cudaError_t launch_stream(const StreamArgs& a, bool fill, int nblocks, cudaStream_t st);
+constexpr int kStreamThreads = 256;
+
+// pair.cuh -- harmonic accumulation over the (primary, bin) lists
+struct AlmArgs {
+  const uint4* pts;               // sorted points
+  const uint32_t* prim;           // sorted positions of the primaries (NULL: identity)
+  int64_t prim_begin;
+  int64_t prim_count;
+  const uint32_t* counts;         // [prim_count][nbins]
+  const uint32_t* offsets;        // [prim_count][nbins]
+  const uint32_t* lists;
+  float* M;                       // [prim_count][nbins][row]
+  const float* norm;              // [row]
+  unsigned long long* work;
+  int nbins;
+  int row;
   float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];  // recurrence beta_lm at [l*(kLmaxCap+1)+m]
 };
-int pair_max_blocks_per_sm(int lmax_kernel, int warps_per_block);
-cudaError_t launch_pair(const PairArgs& a, int lmax_kernel, int warps_per_block, int nblocks,
-                        cudaStream_t st);
+int alm_blocks_per_sm(int lmax_kernel, int warps_per_block);
+cudaError_t launch_alm(const AlmArgs& a, int lmax_kernel, int warps_per_block, int nblocks, cudaStream_t st);
 
 // contract.cu
 struct ContractArgs {

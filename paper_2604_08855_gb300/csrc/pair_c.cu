@@ -2,8 +2,8 @@
 #include "pair.cuh"
 
 namespace ctb {
-template cudaError_t launch_pair_L<9>(const PairArgs&, int, int, cudaStream_t);
-template int pair_occupancy_L<9>(int);
-template cudaError_t launch_pair_L<10>(const PairArgs&, int, int, cudaStream_t);
-template int pair_occupancy_L<10>(int);
+template cudaError_t launch_alm_L<9>(const AlmArgs&, int, int, cudaStream_t);
+template int alm_occupancy_L<9>(int);
+template cudaError_t launch_alm_L<10>(const AlmArgs&, int, int, cudaStream_t);
+template int alm_occupancy_L<10>(int);
 }  // namespace ctb

@@ -2,8 +2,8 @@
 #include "pair.cuh"
 
 namespace ctb {
-template cudaError_t launch_pair_L<12>(const PairArgs&, int, int, cudaStream_t);
-template int pair_occupancy_L<12>(int);
-template cudaError_t launch_pair_L<14>(const PairArgs&, int, int, cudaStream_t);
-template int pair_occupancy_L<14>(int);
+template cudaError_t launch_alm_L<12>(const AlmArgs&, int, int, cudaStream_t);
+template int alm_occupancy_L<12>(int);
+template cudaError_t launch_alm_L<14>(const AlmArgs&, int, int, cudaStream_t);
+template int alm_occupancy_L<14>(int);
 }  // namespace ctb

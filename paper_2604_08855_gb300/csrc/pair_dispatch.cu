@@ -8,9 +8,9 @@ namespace ctb {
 
 // explicit instantiations live in pair_[a-f].cu
 template <int L>
-cudaError_t launch_pair_L(const PairArgs&, int, int, cudaStream_t);
+cudaError_t launch_alm_L(const AlmArgs&, int, int, cudaStream_t);
 template <int L>
-int pair_occupancy_L(int);
+int alm_occupancy_L(int);
 
 void make_layout(int L, Layout* out) {
   Layout& y = *out;
@@ -67,11 +67,11 @@ double norm_lm(int l, int m) {
   return c;
 }
 
-int pair_max_blocks_per_sm(int L, int wpb) {
+int alm_blocks_per_sm(int L, int wpb) {
   switch (L) {
 #define CASE(X) \
   case X:       \
-    return pair_occupancy_L<X>(wpb);
+    return alm_occupancy_L<X>(wpb);
     CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
     CASE(12) CASE(14) CASE(16) CASE(18) CASE(20)
 #undef CASE
@@ -80,11 +80,11 @@ int pair_max_blocks_per_sm(int L, int wpb) {
   }
 }
 
-cudaError_t launch_pair(const PairArgs& a, int L, int wpb, int nblocks, cudaStream_t st) {
+cudaError_t launch_alm(const AlmArgs& a, int L, int wpb, int nblocks, cudaStream_t st) {
   switch (L) {
 #define CASE(X) \
   case X:       \
-    return launch_pair_L<X>(a, wpb, nblocks, st);
+    return launch_alm_L<X>(a, wpb, nblocks, st);
     CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
     CASE(12) CASE(14) CASE(16) CASE(18) CASE(20)
 #undef CASE

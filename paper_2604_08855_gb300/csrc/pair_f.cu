@@ -2,6 +2,6 @@
 #include "pair.cuh"
 
 namespace ctb {
-template cudaError_t launch_pair_L<20>(const PairArgs&, int, int, cudaStream_t);
-template int pair_occupancy_L<20>(int);
+template cudaError_t launch_alm_L<20>(const AlmArgs&, int, int, cudaStream_t);
+template int alm_occupancy_L<20>(int);
 }  // namespace ctb

@@ -214,9 +214,9 @@ class CTB:
         return z
 
     def timings(self):
-        """ms per stage: ingest, sort+grid, pair, pack, contraction, reduce."""
-        buf = (ctypes.c_double * 6)()
-        k = self._check(self.lib.ctb_get_timings(self._h, ctypes.cast(buf, ctypes.c_void_p), 6))
+        """ms per stage: ingest, sort+grid, pair, pack, contraction, reduce, enumeration, accumulation."""
+        buf = (ctypes.c_double * 8)()
+        k = self._check(self.lib.ctb_get_timings(self._h, ctypes.cast(buf, ctypes.c_void_p), 8))
         return list(buf)[:k]
 
     def launch_count(self) -> int:
