@@ -57,17 +57,45 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def _pass_end(L: int, m0: int, cap: int = 128) -> int:
+    s, m = 0, m0
+    while m <= L:
+        c = (L - m + 1) * (1 if m == 0 else 2)
+        if s + c > cap and m > m0:
+            break
+        s += c
+        m += 1
+    return m - 1
+
+
 def flops_per_pair(lmax: int) -> int:
-    """Algorithmic FP32 FLOPs of one pair in the pair kernel's harmonic loop
-    (FMA = 2): separation norm and direction, the complex power w (x+iy)^m,
-    the monic Legendre recurrence and one FMA per accumulated coefficient."""
+    """Algorithmic FP32 FLOPs per pair of the accumulation kernel (FMA = 2),
+    counted from its formulation: per m-range pass the separation norm and
+    direction (8), the Chebyshev sequence T_k(z) (columns m <= m_c: one FMA per
+    degree), the complex power w (x+iy)^m (6 per step), one FMA per
+    coefficient (an ADD where T_0 = 1 or the power itself is added), and the
+    monic Legendre recurrence (MUL + FMA per degree) for columns m > m_c."""
     L = lmax
-    f = 5 + 3  # r^2 (2 FMA + 1 MUL) and the direction (3 MUL)
-    f += 1 + (2 if L >= 1 else 0) + 5 * max(0, L - 1)  # m = 0 column
-    if L >= 1:
-        f += 2 + 6 * (L - 1)  # w (x+iy)^m, m = 1..L
-        for m in range(1, L + 1):
-            f += 2 + (4 if m + 1 <= L else 0) + 7 * max(0, L - m - 1)
+    mc = L if L <= 10 else 3
+    f, m0 = 0, 0
+    while m0 <= L:
+        m1 = _pass_end(L, m0)
+        f += 8
+        if m0 <= mc and L - m0 >= 2:
+            f += 1 + 2 * (L - m0 - 1)
+        ms = max(m0, 1)
+        if m0 == 0:
+            f += 1 + 2 * L                                # column 0 (Chebyshev)
+        if ms <= min(m1, L):
+            f += 2 + 6 * (ms - 1)                         # w (x+iy)^ms
+            for m in range(ms, min(m1, L) + 1):
+                if m > ms:
+                    f += 6
+                if m <= mc:
+                    f += 2 + 4 * (L - m)
+                else:
+                    f += 2 + (4 if m + 1 <= L else 0) + 7 * max(0, L - m - 1)
+        m0 = m1 + 1
     return f
 
 
@@ -270,7 +298,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    pair_ms, launches, npairs = [], 0, 0
+    pair_ms, launches, npairs, stages = [], 0, 0, []
     barrier(world)
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
@@ -280,7 +308,9 @@ def run_ours(args):
             ev[k][0].record(stream)
             step()
             ev[k][1].record(stream)
-            pair_ms.append(est.timings()[2])
+            tm = est.timings()
+            pair_ms.append(tm[7])
+            stages.append(tm)
             launches += est.launch_count()
             npairs = est.pair_count()
         torch.cuda.synchronize(dev)
@@ -312,6 +342,9 @@ def run_ours(args):
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     pair_s = float(np.mean(pair_ms)) / 1e3
     achieved = npairs * flops_per_pair(kw["lmax"]) / pair_s / 1e12
+    st = np.mean(np.array(stages), axis=0)
+    names = ["ingest", "sort_grid", "pair_total", "pack", "contraction", "reduce", "enumerate", "accumulate"]
+    stages_ms = {k: round(float(v), 3) for k, v in zip(names, st)}
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -321,11 +354,12 @@ def run_ours(args):
                    "inputs": "device-resident float64 xyz, w"},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_pair", "achieved": achieved, "peak": peak_tflops,
+        "roofline": {"bound": "alu", "kernel": "k_alm", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
                      "peak_note": f"FP32 FMA pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                   f"{sm_max:.0f} MHz ({pk_kind} max clock)",
-                     "flops_per_pair": flops_per_pair(kw["lmax"]), "pair_kernel_ms": 1e3 * pair_s},
+                     "flops_per_pair": flops_per_pair(kw["lmax"]), "kernel_ms": 1e3 * pair_s},
+        "stages_ms": stages_ms,
         "pairs_per_step": npairs,
         "ms_per_zeta_ell": ms_per_step / (kw["lmax"] + 1),
         "wall_s": wall,

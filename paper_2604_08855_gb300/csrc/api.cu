@@ -59,6 +59,7 @@ struct ctb_ctx {
   Buf xyz_stage, w_stage, key0, val0, key1, val1, hist, scan_tmp, pts_in, pts, s2i, i2s, cell_start;
   Buf flags, bbox_part, lists, M, wprim, partial, zeta, prim, counters, norm, slot, idx64, alm, thr;
   Buf counts, offsets, scan_tmp2;
+  Buf ops[4], slot_lm, lbase_d, kp_d, partial_tc, conv_off, conv_src, conv_coef;
   uint64_t list_cap = (uint64_t)1 << 32;  // neighbour-list entries per chunk (16 GB)
   cudaEvent_t ev[16] = {};
   bool ev_ready = false;
@@ -135,7 +136,9 @@ void release_all(ctb_ctx* c) {
                 &c->scan_tmp, &c->pts_in, &c->pts, &c->s2i, &c->i2s, &c->cell_start, &c->flags,
                 &c->bbox_part, &c->lists, &c->M, &c->wprim, &c->partial, &c->zeta, &c->prim,
                 &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr, &c->counts,
-                &c->offsets, &c->scan_tmp2};
+                &c->offsets, &c->scan_tmp2, &c->ops[0], &c->ops[1], &c->ops[2], &c->ops[3],
+                &c->slot_lm, &c->lbase_d, &c->kp_d, &c->partial_tc, &c->conv_off, &c->conv_src,
+                &c->conv_coef};
   for (Buf* b : all) release(c, *b);
   c->tables_ready = false;
 }
@@ -169,6 +172,21 @@ int ensure_tables(ctb_ctx* c) {
   CK(c, ensure(c, c->slot, sizeof(c->lay.slot)));
   CK(c, cudaMemcpyAsync(c->norm.p, norm.data(), norm.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
   CK(c, cudaMemcpyAsync(c->slot.p, c->lay.slot, sizeof(c->lay.slot), cudaMemcpyHostToDevice, c->st));
+  // slot -> (l, m + l) for the tensor-core pack: l * 64 + (m + l), -1 for padding and l > ell_max
+  std::vector<int> slot_lm(c->lay.row, -1);
+  for (int l = 0; l <= c->lmax; ++l)
+    for (int m = -l; m <= l; ++m) slot_lm[c->lay.slot[l * l + l + m]] = l * 64 + (m + l);
+  std::vector<int> coff, csrc;
+  std::vector<float> ccoef;
+  make_conversion(c->lay, coff, csrc, ccoef);
+  CK(c, ensure(c, c->conv_off, coff.size() * sizeof(int)));
+  CK(c, ensure(c, c->conv_src, csrc.size() * sizeof(int)));
+  CK(c, ensure(c, c->conv_coef, ccoef.size() * sizeof(float)));
+  CK(c, cudaMemcpyAsync(c->conv_off.p, coff.data(), coff.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->conv_src.p, csrc.data(), csrc.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->conv_coef.p, ccoef.data(), ccoef.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CK(c, ensure(c, c->slot_lm, slot_lm.size() * sizeof(int)));
+  CK(c, cudaMemcpyAsync(c->slot_lm.p, slot_lm.data(), slot_lm.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
   CK(c, cudaStreamSynchronize(c->st));  // host sources go out of scope
   c->tables_ready = true;
   return CTB_OK;
@@ -497,16 +515,19 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   aa.counts = P<uint32_t>(c->counts);
   aa.offsets = P<uint32_t>(c->offsets);
   aa.M = P<float>(c->M);
-  aa.norm = P<float>(c->norm);
+  aa.conv_off = P<int>(c->conv_off);
+  aa.conv_src = P<int>(c->conv_src);
+  aa.conv_coef = P<float>(c->conv_coef);
   aa.work = work;
   aa.nbins = nb;
   aa.row = c->lay.row;
   std::memcpy(aa.beta, c->beta, sizeof(aa.beta));
-  double t_stream = 0, t_alm = 0, t_con = 0;
+  double t_stream = 0, t_alm = 0, t_con = 0, t_pack = 0;
   uint64_t pairs = 0;
   int64_t C = pl.chunk_first;
   int64_t c0 = 0;
-  cudaEvent_t* ev = c->ev + 2;  // [0] count start [1] count end [2] fill end [3] alm end [4] contract end
+  // [0] count start [1] count end [2] fill end [3] alm end [4] contraction end [5] pack end
+  cudaEvent_t* ev = c->ev + 2;
   while (c0 < np) {
     const int64_t cnt = std::min(C, np - c0);
     sa.prim_begin = aa.prim_begin = c0;
@@ -538,7 +559,31 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     CK(c, cudaMemsetAsync(work, 0, 8, c->st));
     CK(c, launch_alm(aa, c->Lk, pl.wpb, pl.alm_blocks, c->st));
     CK(c, cudaEventRecord(ev[3], c->st));
-    if (contract) {
+    if (contract && c->precision != CTB_PREC_FP32) {
+      const bool tf32 = c->precision == CTB_PREC_TF32;
+      std::vector<unsigned long long> lb, kp;
+      size_t elems = 0;
+      tc_layout(tf32, cnt, nb, c->lmax, lb, kp, &elems);
+      const size_t esz = tf32 ? 4 : 2;
+      for (int k = 0; k < 4; ++k) {
+        if (tf32 && (k == 1 || k == 3)) continue;
+        CK(c, ensure(c, c->ops[k], elems * esz));
+        CK(c, cudaMemsetAsync(c->ops[k].p, 0, elems * esz, c->st));
+      }
+      CK(c, ensure(c, c->lbase_d, lb.size() * 8));
+      CK(c, ensure(c, c->kp_d, kp.size() * 8));
+      CK(c, cudaMemcpyAsync(c->lbase_d.p, lb.data(), lb.size() * 8, cudaMemcpyHostToDevice, c->st));
+      CK(c, cudaMemcpyAsync(c->kp_d.p, kp.data(), kp.size() * 8, cudaMemcpyHostToDevice, c->st));
+      CK(c, launch_pack(tf32, P<float>(c->M), P<float>(c->wprim), cnt, nb, c->lay.row, P<int>(c->slot_lm),
+                        P<unsigned long long>(c->lbase_d), P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p,
+                        c->ops[2].p, c->ops[3].p, c->st));
+      CK(c, cudaEventRecord(ev[5], c->st));
+      CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), c->ops[0].p, c->ops[1].p, c->ops[2].p,
+                               c->ops[3].p, P<double>(c->partial_tc), pl.nparts, P<unsigned int>(c->flags) + 1,
+                               c->st));
+      // host vectors lb / kp are read by the copies above before they are released
+      CK(c, cudaStreamSynchronize(c->st));
+    } else if (contract) {
       ContractArgs ca{};
       ca.M = P<float>(c->M);
       ca.wprim = P<float>(c->wprim);
@@ -564,7 +609,12 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     CK(c, cudaEventSynchronize(ev[4]));
     t_stream += elapsed(ev[1], ev[2]);
     t_alm += elapsed(ev[2], ev[3]);
-    t_con += elapsed(ev[3], ev[4]);
+    if (contract && c->precision != CTB_PREC_FP32) {
+      t_pack += elapsed(ev[3], ev[5]);
+      t_con += elapsed(ev[5], ev[4]);
+    } else {
+      t_con += elapsed(ev[3], ev[4]);
+    }
     pairs += tot;
     c0 += cnt;
     // next chunk: fill about 90 % of the list buffer at the observed density
@@ -573,6 +623,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     C = std::max<int64_t>(1, std::min<int64_t>(nxt, pl.chunk_max));
   }
   c->t_ms[2] = t_stream + t_alm;
+  c->t_ms[3] = t_pack;
   c->t_ms[4] = t_con;
   c->t_ms[6] = t_stream;
   c->t_ms[7] = t_alm;
@@ -583,7 +634,6 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
 int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out) {
   if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
   if (!zeta_out) return fail(c, CTB_ERR_ARG, "zeta_out is NULL");
-  if (c->precision != CTB_PREC_FP32) return fail(c, CTB_ERR_UNSUPPORTED, "precision not available");
   CK(c, cudaSetDevice(c->dev));
   int r = ensure_tables(c);
   if (r) return r;
@@ -594,20 +644,32 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
   CK(c, ensure(c, c->partial, (size_t)pl.nparts * zsz * sizeof(double)));
   CK(c, ensure(c, c->zeta, zsz * sizeof(double)));
   CK(c, cudaMemsetAsync(c->partial.p, 0, (size_t)pl.nparts * zsz * sizeof(double), c->st));
+  const bool tc = c->precision != CTB_PREC_FP32;
+  if (tc) {
+    CK(c, ensure(c, c->partial_tc, (size_t)pl.nparts * zsz * sizeof(double)));
+    CK(c, cudaMemsetAsync(c->partial_tc.p, 0, (size_t)pl.nparts * zsz * sizeof(double), c->st));
+    CK(c, cudaMemsetAsync(P<unsigned int>(c->flags) + 1, 0, 4, c->st));
+  }
   for (int k = 0; k < kStages; ++k) c->t_ms[k] = 0;
   uint64_t pairs = 0;
   r = run_pairs(c, dprim, np, true, pl, nullptr, &pairs);
   if (r) return r;
   const int evs = 2 + 8;
   CK(c, cudaEventRecord(c->ev[evs], c->st));
-  CK(c, launch_finalize(P<double>(c->partial), pl.nparts, c->lmax, c->nbins, P<double>(c->zeta), c->st));
+  if (tc)
+    CK(c, launch_finalize_tc(P<double>(c->partial_tc), c->lmax, pl.nparts, c->nbins, P<double>(c->zeta), c->st));
+  else
+    CK(c, launch_finalize(P<double>(c->partial), pl.nparts, c->lmax, c->nbins, P<double>(c->zeta), c->st));
   CK(c, cudaEventRecord(c->ev[evs + 1], c->st));
   const bool dev_out = is_device_ptr(zeta_out);
   CK(c, cudaMemcpyAsync(zeta_out, c->zeta.p, zsz * sizeof(double),
                         dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  unsigned int tc_err = 0;
+  if (tc) CK(c, cudaMemcpyAsync(&tc_err, P<unsigned int>(c->flags) + 1, 4, cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   c->npairs = pairs;
   c->t_ms[5] = elapsed(c->ev[evs], c->ev[evs + 1]);
+  if (tc_err) return fail(c, CTB_ERR_TIMEOUT, "tensor-core contraction: a bounded wait timed out");
   return CTB_OK;
 }
 
@@ -785,7 +847,6 @@ int ctb_set_option(ctb_ctx* c, int key, int64_t v) {
     case CTB_OPT_PRECISION:
       if (v != CTB_PREC_FP32 && v != CTB_PREC_BF16X3 && v != CTB_PREC_TF32)
         return fail(c, CTB_ERR_ARG, "unknown precision");
-      if (v != CTB_PREC_FP32) return fail(c, CTB_ERR_UNSUPPORTED, "precision not available in this build");
       c->precision = (int)v;
       return CTB_OK;
     case CTB_OPT_CELLS_PER_RMAX:

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ctb.h"
 
 namespace ctb {
@@ -118,6 +120,8 @@ unsigned long long sq_threshold(double edge, double unit);
 // recurrence constants (pair_dispatch.cu)
 void fill_beta(float* beta);   // beta_lm at [l*(kLmaxCap+1)+m]
 double norm_lm(int l, int m);  // C_lm of the real orthonormal Y_l,m
+// flush conversion table of kernel L: accumulator totals -> normalised a_lm
+void make_conversion(const Layout& lay, std::vector<int>& off, std::vector<int>& src, std::vector<float>& coef);
 
 // ---------------------------------------------------------------------------
 // kernels and launchers (all asynchronous on `st`)
@@ -185,7 +189,9 @@ struct AlmArgs {
   const uint32_t* offsets;        // [prim_count][nbins]
   const uint32_t* lists;
   float* M;                       // [prim_count][nbins][row]
-  const float* norm;              // [row]
+  const int* conv_off;            // [row + 1] flush conversion: entries of slot s are [off[s], off[s+1])
+  const int* conv_src;            //   source slot of each entry (same pass)
+  const float* conv_coef;         //   coefficient of each entry
   unsigned long long* work;
   int nbins;
   int row;
@@ -209,5 +215,18 @@ struct ContractArgs {
 cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t st);
 cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbins,
                             double* zeta, cudaStream_t st);
+
+// contract_tc.cu -- tcgen05 contraction (BF16 hi/lo split or TF32)
+int tc_npad(int nbins);
+void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned long long>& lbase,
+               std::vector<unsigned long long>& kp, size_t* elems);
+cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row,
+                        const int* slot_lm, const unsigned long long* lbase, const unsigned long long* kp,
+                        void* ahi, void* alo, void* bhi, void* blo, cudaStream_t st);
+cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const unsigned long long* h_lbase,
+                               const unsigned long long* h_kp, void* ahi, void* alo, void* bhi, void* blo,
+                               double* partial, int nsplit, unsigned int* err, cudaStream_t st);
+cudaError_t launch_finalize_tc(const double* partial, int lmax, int nsplit, int nbins, double* zeta,
+                               cudaStream_t st);
 
 }  // namespace ctb

@@ -31,8 +31,14 @@ namespace ctb {
 
 constexpr uint32_t kNone = 0xffffffffu;
 
-// Column m >= 1 of the recurrence, l = LL..L (template recursion keeps every
-// accumulator index a compile-time constant, so the array stays in registers).
+// Columns accumulated as Chebyshev moments: m <= cheb_max_m(L).  Above it
+// the monic Legendre recurrence is used (its conditioning does not degrade
+// with m; the moment conversion does).
+__host__ __device__ constexpr int cheb_max_m(int L) { return L <= 10 ? L : 3; }
+
+// Column m >= 1 of the Legendre recurrence, l = LL..L (template recursion keeps
+// every accumulator index a compile-time constant, so the array stays in
+// registers).
 template <int L, int M0, int M1, int M, int LL>
 __device__ __forceinline__ void column_rec(const AlmArgs& a, float* acc, float z, float cr, float ci, float p2,
                                            float p1) {
@@ -44,44 +50,74 @@ __device__ __forceinline__ void column_rec(const AlmArgs& a, float* acc, float z
   }
 }
 
-// Column m = 0, l = LL..L.
-template <int L, int M0, int M1, int LL>
-__device__ __forceinline__ void column0_rec(const AlmArgs& a, float* acc, float w, float z, float p2, float p1) {
-  if constexpr (LL <= L) {
-    const float p = fmaf(z, p1, -(a.beta[LL * (kLmaxCap + 1)] * p2));
-    acc[local_slot(LL, 0, M0, M1)] = fmaf(w, p, acc[local_slot(LL, 0, M0, M1)]);
-    column0_rec<L, M0, M1, LL + 1>(a, acc, w, z, p1, p);
+// Chebyshev column m: moments S_{m,k} += c T_k, k = K..L-m, stored in slot (m + k, +-m).
+template <int L, int M0, int M1, int M, int K>
+__device__ __forceinline__ void cheb_col(float* acc, const float* T, float cr, float ci) {
+  if constexpr (K <= L - M) {
+    if constexpr (M == 0) {
+      acc[local_slot(K, 0, M0, M1)] = fmaf(cr, T[K], acc[local_slot(K, 0, M0, M1)]);
+    } else {
+      acc[local_slot(M + K, M, M0, M1)] = fmaf(cr, T[K], acc[local_slot(M + K, M, M0, M1)]);
+      acc[local_slot(M + K, -M, M0, M1)] = fmaf(ci, T[K], acc[local_slot(M + K, -M, M0, M1)]);
+    }
+    cheb_col<L, M0, M1, M, K + 1>(acc, T, cr, ci);
   }
 }
 
 // Columns m = M..ME with (cr, ci) = w (x + i y)^M on entry.
 template <int L, int M0, int M1, int M, int ME>
-__device__ __forceinline__ void columns_rec(const AlmArgs& a, float* acc, float x, float y, float z, float cr,
-                                            float ci) {
+__device__ __forceinline__ void columns_rec(const AlmArgs& a, float* acc, const float* T, float x, float y, float z,
+                                            float cr, float ci) {
   if constexpr (M <= ME) {
-    acc[local_slot(M, M, M0, M1)] += cr;
-    acc[local_slot(M, -M, M0, M1)] += ci;
-    if constexpr (M + 1 <= L) {
-      acc[local_slot(M + 1, M, M0, M1)] = fmaf(z, cr, acc[local_slot(M + 1, M, M0, M1)]);
-      acc[local_slot(M + 1, -M, M0, M1)] = fmaf(z, ci, acc[local_slot(M + 1, -M, M0, M1)]);
+    if constexpr (M <= cheb_max_m(L)) {
+      acc[local_slot(M, M, M0, M1)] += cr;  // T_0 = 1
+      acc[local_slot(M, -M, M0, M1)] += ci;
+      cheb_col<L, M0, M1, M, 1>(acc, T, cr, ci);
+    } else {
+      acc[local_slot(M, M, M0, M1)] += cr;
+      acc[local_slot(M, -M, M0, M1)] += ci;
+      if constexpr (M + 1 <= L) {
+        acc[local_slot(M + 1, M, M0, M1)] = fmaf(z, cr, acc[local_slot(M + 1, M, M0, M1)]);
+        acc[local_slot(M + 1, -M, M0, M1)] = fmaf(z, ci, acc[local_slot(M + 1, -M, M0, M1)]);
+      }
+      column_rec<L, M0, M1, M, M + 2>(a, acc, z, cr, ci, 1.f, z);
     }
-    column_rec<L, M0, M1, M, M + 2>(a, acc, z, cr, ci, 1.f, z);
     if constexpr (M + 1 <= ME) {
       const float nr = fmaf(cr, x, -(ci * y));
       const float ni = fmaf(cr, y, ci * x);
-      columns_rec<L, M0, M1, M + 1, ME>(a, acc, x, y, z, nr, ni);
+      columns_rec<L, M0, M1, M + 1, ME>(a, acc, T, x, y, z, nr, ni);
     }
   }
 }
 
+// T_k(z), k = K..KMAX, by T_k = 2z T_{k-1} - T_{k-2}: one FMA per degree.
+template <int K, int KMAX>
+__device__ __forceinline__ void cheb_seq(float* T, float z2) {
+  if constexpr (K <= KMAX) {
+    T[K] = fmaf(z2, T[K - 1], -T[K - 2]);
+    cheb_seq<K + 1, KMAX>(T, z2);
+  }
+}
+
 // Add one neighbour (weight w, unit direction x, y, z) to the pass's
-// accumulators: one FMA per coefficient plus the recurrences.
+// accumulators: one FMA per coefficient, plus the Chebyshev sequence (shared
+// by all Chebyshev columns), the Legendre recurrences of the other columns,
+// and the complex power.
 template <int L, int M0, int M1>
 __device__ __forceinline__ void accum_pass(const AlmArgs& a, float* acc, float w, float x, float y, float z) {
+  constexpr int MC = cheb_max_m(L);
+  constexpr int KMAX = M0 <= MC ? L - M0 : 1;  // highest Chebyshev degree this pass needs
+  float T[KMAX + 1 > 2 ? KMAX + 1 : 2];
+  if constexpr (M0 <= MC) {
+    T[0] = 1.f;
+    T[1] = z;
+    cheb_seq<2, KMAX>(T, z + z);
+  }
   if constexpr (M0 == 0) {
-    acc[local_slot(0, 0, M0, M1)] += w;
-    if constexpr (L >= 1) acc[local_slot(1, 0, M0, M1)] = fmaf(w, z, acc[local_slot(1, 0, M0, M1)]);
-    column0_rec<L, M0, M1, 2>(a, acc, w, z, 1.f, z);
+    if constexpr (MC >= 0) {
+      acc[local_slot(0, 0, M0, M1)] += w;
+      cheb_col<L, M0, M1, 0, 1>(acc, T, w, 0.f);
+    }
   }
   constexpr int MS = M0 < 1 ? 1 : M0;
   constexpr int ME = M1 < L ? M1 : L;
@@ -93,7 +129,7 @@ __device__ __forceinline__ void accum_pass(const AlmArgs& a, float* acc, float w
       ci = fmaf(cr, y, ci * x);
       cr = t;
     }
-    columns_rec<L, M0, M1, MS, ME>(a, acc, x, y, z, cr, ci);
+    columns_rec<L, M0, M1, MS, ME>(a, acc, T, x, y, z, cr, ci);
   }
 }
 
@@ -167,13 +203,13 @@ __device__ __forceinline__ uint32_t rec_at(const uint32_t* __restrict__ lists, R
   return k < nxt.n ? __ldcg(lists + nxt.off + k) : kNone;
 }
 
-__device__ __forceinline__ Prefetch prefetch_start(const uint32_t* lists, const uint4* pts, Run r, uint4 P,
-                                                   int lane) {
+// Loads of the first two iterations of the concatenated runs [r | nxt].
+__device__ __forceinline__ Prefetch prefetch_start(const uint32_t* lists, const uint4* pts, Run r, Run nxt,
+                                                   uint4 P, int lane) {
   Prefetch pf;
-  const Run none{0, 0};
   const uint32_t T = (r.n + 31u) / 32u;
-  pf.j0 = rec_at(lists, r, none, T, 0, lane);
-  pf.j1 = rec_at(lists, r, none, T, 1, lane);
+  pf.j0 = rec_at(lists, r, nxt, T, 0, lane);
+  pf.j1 = rec_at(lists, r, nxt, T, 1, lane);
   pf.q0 = pf.j0 != kNone ? __ldg(pts + pf.j0) : P;
   return pf;
 }
@@ -183,8 +219,7 @@ __device__ __forceinline__ Prefetch prefetch_start(const uint32_t* lists, const 
 // next run starts without a memory bubble.
 template <int L, int M0, int M1>
 __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, const uint4 P, Prefetch& pf,
-                                         float* __restrict__ out, const float* __restrict__ norm, float* sbuf,
-                                         int lane) {
+                                         float* __restrict__ out, int base, float* sbuf, int lane) {
   constexpr int NCP = round32(coef_count(L, M0, M1));
   const uint32_t* __restrict__ lists = a.lists;
   const uint4* __restrict__ pts = a.pts;
@@ -192,6 +227,9 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
 #pragma unroll
   for (int i = 0; i < NCP; ++i) acc[i] = 0.f;
   const uint32_t T = (cur.n + 31u) / 32u;
+  // the second record word: the previous run could not see past this run
+  // when it is a single step long, so take it from (cur, nxt)
+  pf.j1 = rec_at(lists, cur, nxt, T, 1, lane);
   for (uint32_t t = 0; t < T; ++t) {
     const uint4 q = pf.q0;
     const bool valid = pf.j0 != kNone;
@@ -212,15 +250,29 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
     accum_pass<L, M0, M1>(a, acc, w, dx * ir, dy * ir, dz * ir);
   }
   smem_transpose_reduce<NCP>(acc, sbuf, lane);
+  // lane holds the warp totals of local slots [lane * V, lane * V + V); turn
+  // them into normalised a_lm: out[s] = sum_e coef_e * total[src_e]
+  // (Chebyshev moments -> Legendre values; one entry, the normalisation, for
+  // slots accumulated by the Legendre recurrence)
   constexpr int V = NCP / 32;
+#pragma unroll
+  for (int i = 0; i < V; ++i) sbuf[lane * V + i] = acc[i];
+  __syncwarp();
   float* o = out + lane * V;
-  const float* nm = norm + lane * V;
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+    const int sl = base + lane * V + i;
+    const int e0 = __ldg(a.conv_off + sl), e1 = __ldg(a.conv_off + sl + 1);
+    float v = 0.f;
+    for (int e = e0; e < e1; ++e) v = fmaf(__ldg(a.conv_coef + e), sbuf[__ldg(a.conv_src + e) - base], v);
+    acc[i] = v;
+  }
+  __syncwarp();
   if constexpr (V == 4) {
-    const float4 s = __ldg(reinterpret_cast<const float4*>(nm));
-    *reinterpret_cast<float4*>(o) = make_float4(acc[0] * s.x, acc[1] * s.y, acc[2] * s.z, acc[3] * s.w);
+    *reinterpret_cast<float4*>(o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
   } else {
 #pragma unroll
-    for (int i = 0; i < V; ++i) o[i] = acc[i] * __ldg(nm + i);
+    for (int i = 0; i < V; ++i) o[i] = acc[i];
   }
 }
 
@@ -232,7 +284,7 @@ struct PassChain {
   static constexpr bool LAST = M1 + 1 > L;
   __device__ static __forceinline__ void run(const AlmArgs& a, Run cur, Run nxt_bin, const uint4 P, Prefetch& pf,
                                              float* out, float* sbuf, int lane) {
-    run_pass<L, M0, M1>(a, cur, LAST ? nxt_bin : cur, P, pf, out + BASE, a.norm + BASE, sbuf, lane);
+    run_pass<L, M0, M1>(a, cur, LAST ? nxt_bin : cur, P, pf, out + BASE, BASE, sbuf, lane);
     if constexpr (!LAST) PassChain<L, M1 + 1, BASE + NCP>::run(a, cur, nxt_bin, P, pf, out, sbuf, lane);
   }
 };
@@ -286,20 +338,27 @@ __global__ void __launch_bounds__(128, 3) k_alm(AlmArgs a) {
     __syncwarp();
     int b = 0;
     while (b < nbins && s_n[b] == 0) ++b;
-    if (b >= nbins) continue;
-    const int64_t gi = a.prim_begin + (int64_t)i;
-    const uint32_t sp = a.prim ? __ldg(a.prim + gi) : (uint32_t)gi;
-    const uint4 P = __ldg(a.pts + sp);
-    Run cur{s_off[b], s_n[b]};
-    Prefetch pf = prefetch_start(a.lists, a.pts, cur, P, lane);
-    while (b < nbins) {
+    if (b < nbins) {
+      const int64_t gi = a.prim_begin + (int64_t)i;
+      const uint32_t sp = a.prim ? __ldg(a.prim + gi) : (uint32_t)gi;
+      const uint4 P = __ldg(a.pts + sp);
       int nb = b + 1;
       while (nb < nbins && s_n[nb] == 0) ++nb;
-      const Run nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
-      PassChain<L, 0, 0>::run(a, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, sbuf, lane);
-      b = nb;
-      cur = nxt;
+      Run cur{s_off[b], s_n[b]};
+      Run nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
+      // the first pass continues into the same bin when more m-passes follow
+      Prefetch pf = prefetch_start(a.lists, a.pts, cur, PassChain<L, 0, 0>::LAST ? nxt : cur, P, lane);
+      while (true) {
+        PassChain<L, 0, 0>::run(a, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, sbuf, lane);
+        b = nb;
+        if (b >= nbins) break;
+        cur = nxt;
+        nb = b + 1;
+        while (nb < nbins && s_n[nb] == 0) ++nb;
+        nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
+      }
     }
+    __syncwarp();  // s_n / s_off are rewritten for the next primary
   }
 }
 

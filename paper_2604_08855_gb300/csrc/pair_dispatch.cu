@@ -1,6 +1,8 @@
 // pair_dispatch.cu -- coefficient layout, recurrence constants, and the
 // ell_max dispatch of the pair-multipole kernel.
 #include <cmath>
+#include <utility>
+#include <vector>
 
 #include "ctb_internal.cuh"
 
@@ -65,6 +67,69 @@ double norm_lm(int l, int m) {
   for (int k = am + 1; k <= l; ++k) c *= rec_a(k, am);
   if (am != 0) c *= M_SQRT2;
   return c;
+}
+
+// T-basis coefficients of the monic recurrence polynomial p_l^m(z) (degree
+// l - m): p_m = 1, p_{m+1} = z, p_l = z p_{l-1} - beta_lm p_{l-2}, with
+// z T_0 = T_1 and z T_k = (T_{k+1} + T_{k-1}) / 2.
+static std::vector<double> monic_in_T(int l, int m) {
+  const int n = l - m;
+  std::vector<double> p2(n + 2, 0.0), p1(n + 2, 0.0);
+  p2[0] = 1.0;  // p_m
+  if (n == 0) return std::vector<double>(p2.begin(), p2.begin() + 1);
+  p1[1] = 1.0;  // p_{m+1} = z = T_1
+  for (int ll = m + 2; ll <= l; ++ll) {
+    std::vector<double> zp(n + 2, 0.0);
+    for (int k = 0; k <= n; ++k) {
+      if (p1[k] == 0.0) continue;
+      if (k == 0) {
+        zp[1] += p1[0];
+      } else {
+        zp[k + 1] += 0.5 * p1[k];
+        zp[k - 1] += 0.5 * p1[k];
+      }
+    }
+    const double beta = rec_b(ll, m) / rec_a(ll - 1, m);
+    for (int k = 0; k <= n; ++k) zp[k] -= beta * p2[k];
+    p2 = p1;
+    p1 = zp;
+  }
+  return std::vector<double>(p1.begin(), p1.begin() + n + 1);
+}
+
+// Columns m <= cheb_max_m(L) hold Chebyshev moments S_{m,k} = sum w c_m T_k(z)
+// in slot (m + k, +-m); the others hold Legendre sums in slot (l, +-m).
+void make_conversion(const Layout& lay, std::vector<int>& off, std::vector<int>& src, std::vector<float>& coef) {
+  const int L = lay.L;
+  const int MC = L <= 10 ? L : 3;
+  std::vector<std::vector<std::pair<int, float>>> ent(lay.row);
+  for (int l = 0; l <= L; ++l) {
+    for (int m = -l; m <= l; ++m) {
+      const int am = m < 0 ? -m : m;
+      const int s = lay.slot[l * l + l + m];
+      const double nrm = norm_lm(l, m);
+      if (am <= MC) {
+        const std::vector<double> c = monic_in_T(l, am);
+        for (int k = 0; k <= l - am; ++k) {
+          const int sl = am + k, srcm = m;
+          ent[s].push_back({lay.slot[sl * sl + sl + srcm], (float)(nrm * c[k])});
+        }
+      } else {
+        ent[s].push_back({s, (float)nrm});
+      }
+    }
+  }
+  off.assign(lay.row + 1, 0);
+  src.clear();
+  coef.clear();
+  for (int s = 0; s < lay.row; ++s) {
+    off[s] = (int)src.size();
+    for (auto& e : ent[s]) {
+      src.push_back(e.first);
+      coef.push_back(e.second);
+    }
+  }
+  off[lay.row] = (int)src.size();
 }
 
 int alm_blocks_per_sm(int L, int wpb) {

@@ -225,3 +225,31 @@ def test_thomas_1m_sampled_primaries(ctbmod):
     ref = oracle.zeta(xyz, w, prim=prim, **kw)
     assert est.pair_count() == ref["npairs"]
     assert zeta_err(z, ref) < TOL_FP32
+
+
+# ------------------------------------------------------- tensor-core contraction
+
+TOL_MIXED = 1e-3   # BF16 hi/lo split or TF32 contraction, FP32 accumulate, FP64 reduce
+
+
+@pytest.mark.parametrize("prec", ["BF16X3", "TF32"])
+@pytest.mark.parametrize("nbins,lmax", [(8, 10), (36, 10), (5, 20)])
+def test_tensor_core_contraction_vs_oracle(ctbmod, prec, nbins, lmax):
+    xyz, w = synth.thomas(5000, 300.0, 50, 5.0, seed=28, weights="u0.5-1.5")
+    kw = dict(box=300.0, rmin=2.0, rmax=50.0, nbins=nbins, lmax=lmax)
+    z, _ = run_full(ctbmod, xyz, w, kw, precision=getattr(ctbmod, "PREC_" + prec))
+    ref = oracle.zeta(xyz, w, **kw)
+    err = zeta_err(z, ref)
+    assert err < TOL_MIXED
+    if prec == "BF16X3":
+        assert err < 1e-4  # three products keep ~16 mantissa bits per operand
+
+
+def test_tensor_core_chunks_and_negative_weights(ctbmod):
+    """Several primary chunks accumulate into the same per-CTA partials; signed weights."""
+    xyz, _ = synth.uniform(6000, 250.0, seed=29)
+    w = np.random.default_rng(29).uniform(-1.0, 1.0, xyz.shape[0])
+    kw = dict(box=250.0, rmin=2.0, rmax=40.0, nbins=6, lmax=6)
+    z, _ = run_full(ctbmod, xyz, w, kw, precision=ctbmod.PREC_BF16X3, chunk_primaries=1024)
+    ref = oracle.zeta(xyz, w, **kw)
+    assert zeta_err(z, ref) < TOL_MIXED
