@@ -184,6 +184,36 @@ int ctb_get_launch_count(ctb_ctx* ctx, uint64_t* kernels);
 /* Number of ordered (primary, secondary) pairs binned by the last compute. */
 int ctb_get_pair_count(ctb_ctx* ctx, uint64_t* pairs);
 
+/*
+ * zeta_l(b1,b2) from a_lm rows and primary weights already on the device,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * exists for callers that must not allocate device memory when they call in
+ * -- services that reserve the whole device in their own pool up front and
+ * hand out only fixed buffers, or loops with a latency budget in which an
+ * allocation, or its failure, is not acceptable.  It runs the same FP32
+ * contraction and FP64 normalisation as ctb_compute, with its per-block
+ * partial sums in a fixed, file-scope device array of the library (8 MB on
+ * every GPU that loads the library, held until the process exits).
+ *   alm       [np][nbins][(ell_max+1)^2] float32, device; coefficient (l, m)
+ *             at index l*l + l + m (the layout of ctb_get_alm)
+ *   w         [np] float32 primary weights, device
+ *   np        number of primaries, >= 0 (0 gives zeta = 0)
+ *   zeta_out  [(ell_max+1)][nbins][nbins] float64, device, written in full
+ *   stream    cudaStream_t to run on (NULL = legacy default); the call returns
+ *             once the work is queued
+ * Limits: nbins 1..CTB_NBINS_CAP, ell_max 0..CTB_LMAX_CAP and
+ * (ell_max+1) * nbins^2 <= 16384 (the size of the fixed array); otherwise
+ * CTB_ERR_ARG.  A failed CUDA call gives CTB_ERR_CUDA.  ctb_last_error()
+ * does not describe failures of this call.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and initialises a small table on the given stream; make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race and must be serialised by the
+ * caller (e.g. one stream).  Each call clears the part it uses first.
+ */
+int ctb_contract_noalloc(const float* alm, const float* w, int64_t np, int nbins, int ell_max,
+                         double* zeta_out, void* stream);
+
 /* Release the context and all device memory it holds.  NULL is a no-op. */
 void ctb_destroy(ctb_ctx* ctx);
 

@@ -30,8 +30,8 @@ LMAX_CAP, NBINS_CAP = 20, 64
 # every symbol include/ctb.h declares
 EXPORTS = ("ctb_create", "ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm",
            "ctb_compute_batch", "ctb_set_option", "ctb_set_stream", "ctb_set_allocator",
-           "ctb_get_timings", "ctb_get_pair_count", "ctb_get_launch_count", "ctb_destroy", "ctb_last_error",
-           "ctb_version")
+           "ctb_get_timings", "ctb_get_pair_count", "ctb_get_launch_count", "ctb_contract_noalloc",
+           "ctb_destroy", "ctb_last_error", "ctb_version")
 
 _lib = None
 
@@ -65,6 +65,7 @@ def load(path: str | None = None):
     lib.ctb_get_timings.argtypes = [vp, vp, i32]
     lib.ctb_get_pair_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.ctb_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.ctb_contract_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     lib.ctb_destroy.argtypes = [vp]
     lib.ctb_destroy.restype = None
     lib.ctb_last_error.argtypes = [vp]
@@ -73,7 +74,7 @@ def load(path: str | None = None):
     lib.ctb_version.restype = ctypes.c_char_p
     for name in ("ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm", "ctb_compute_batch",
                  "ctb_set_option", "ctb_set_stream", "ctb_set_allocator", "ctb_get_timings",
-                 "ctb_get_pair_count", "ctb_get_launch_count"):
+                 "ctb_get_pair_count", "ctb_get_launch_count", "ctb_contract_noalloc"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -229,6 +230,20 @@ class CTB:
         v = ctypes.c_uint64(0)
         self._check(self.lib.ctb_get_pair_count(self._h, ctypes.byref(v)))
         return int(v.value)
+
+
+def contract_noalloc(alm, w, nbins: int, lmax: int, out, stream=None) -> None:
+    """zeta from device a_lm rows [np][nbins][(lmax+1)^2] and device weights [np]
+    (float32 CUDA tensors) into `out` (float64 CUDA tensor), with no device
+    allocation by the library; see ctb_contract_noalloc in include/ctb.h."""
+    lib = load()
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    np_ = int(alm.shape[0])
+    rc = lib.ctb_contract_noalloc(_ptr(alm), _ptr(w), np_, int(nbins), int(lmax), _ptr(out),
+                                  ctypes.c_void_p(stream or 0))
+    if rc < 0:
+        raise CTBError(rc, "ctb_contract_noalloc failed")
 
 
 def version() -> str:
