@@ -54,6 +54,19 @@ def workload(name: str):
         return xyz, w, synth.config_params(1), {
             "workload": "uniform_20k", "n_points": 20_000, "box": 1000.0, "r_min": 10.0, "r_max": 100.0,
             "nbins": 10, "ell_max": 10, "periodic": True, "weights": "unit"}
+    if name == "cut_sky":
+        xyz, w = synth.cut_sky()
+        return xyz, w, synth.config_params(5), {
+            "workload": "cut_sky", "n_points": 32_000_000, "box": "open", "r_min": 20.0, "r_max": 200.0,
+            "nbins": 36, "ell_max": 10, "periodic": False,
+            "clustering": "8M Thomas data (w=+1) + 24M uniform randoms (w=-1/3) in an RA 0-60, Dec -30..30 deg, "
+                          "r 500-1500 sector"}
+    if name == "thomas_4m":
+        xyz, w = synth.thomas_4m()
+        return xyz, w, synth.config_params(3), {
+            "workload": "thomas_4m", "n_points": 4_000_000, "box": 2000.0, "r_min": 10.0, "r_max": 200.0,
+            "nbins": 32, "ell_max": 20, "periodic": True, "clustering": "Thomas, 40k parents, sigma 5",
+            "weights": "U[0.5,1.5]"}
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -141,9 +141,15 @@ int ctb_get_alm(ctb_ctx* ctx, const int64_t* primary_idx, int64_t m, float* alm_
  * ell_max; catalogue i has n[i] points at xyz[i] (host or device, [n_i][3])
  * and weights w[i] (NULL pointer or NULL array: unit weights).
  *   zeta_out  [k][(ell_max+1)][nbins][nbins] float64, host or device.
- * The context's own catalogue (ctb_set_points) is left unchanged.
- * Errors: CTB_ERR_ARG (k < 1, a NULL xyz[i] with n[i] > 0, n[i] out of
- * range), CTB_ERR_NONFINITE, CTB_ERR_OOM, CTB_ERR_CUDA, CTB_ERR_TIMEOUT.
+ * All catalogues go into one sorted grid (cell key = catalogue * cells +
+ * cell), one pair pipeline runs over every primary with each neighbour search
+ * kept inside its own catalogue, and the contraction keeps one set of FP64
+ * partial sums per catalogue.  The batch replaces the context's catalogue:
+ * call ctb_set_points again before the next ctb_compute.  Periodic boxes only.
+ * Errors: CTB_ERR_ARG (k < 1, a NULL xyz[i] with n[i] > 0, a negative n[i],
+ * more than 2^31 points in total or k * grid cells >= 2^32),
+ * CTB_ERR_UNSUPPORTED (open boundary), CTB_ERR_NONFINITE, CTB_ERR_OOM,
+ * CTB_ERR_CUDA, CTB_ERR_TIMEOUT.
  */
 int ctb_compute_batch(ctb_ctx* ctx, const double* const* xyz, const double* const* w,
                       const int64_t* n, int k, double* zeta_out);
@@ -167,8 +173,9 @@ int ctb_set_allocator(ctb_ctx* ctx, void* (*alloc)(size_t bytes, void* user),
                       void (*free_fn)(void* ptr, void* user), void* user);
 
 /*
- * Per-stage device times of the last ctb_set_points / ctb_compute* call, in
- * milliseconds, measured with CUDA events on the context's stream:
+ * Per-stage device times in milliseconds, measured with CUDA events on the
+ * context's stream: [0], [1] from the last ctb_set_points (or batch), the
+ * others from the last ctb_compute* call:
  *   [0] ingest  [1] sort + grid  [2] pair multipoles (= [6] + [7])  [3] pack
  *   [4] contraction  [5] reduce + normalise
  *   [6] neighbour enumeration (count + scan + fill)  [7] harmonic accumulation

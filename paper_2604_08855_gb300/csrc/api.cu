@@ -61,6 +61,7 @@ struct ctb_ctx {
   Buf counts, offsets, scan_tmp2;
   Buf ops[4], slot_lm, lbase_d, kp_d, partial_tc, conv_off, conv_src, conv_coef;
   uint64_t list_cap = (uint64_t)1 << 32;  // neighbour-list entries per chunk (16 GB)
+  const uint32_t* batch_keys = nullptr;    // sorted keys while a batch is loaded
   cudaEvent_t ev[16] = {};
   bool ev_ready = false;
   double t_ms[kStages] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -277,6 +278,36 @@ unsigned long long ctb::sq_threshold(double edge, double unit) {
 
 namespace {
 
+// exact edges, the same FP64 values an FP64 evaluation of the bins uses:
+// r_min, r_min + b (r_max - r_min)/nbins, r_max
+int upload_thresholds(ctb_ctx* c) {
+  std::vector<unsigned long long> thr(c->nbins + 1);
+  const double dr = (c->rmax - c->rmin) / c->nbins;
+  thr[0] = sq_threshold(c->rmin, c->unit);
+  for (int b = 1; b < c->nbins; ++b) {
+    const double bd = b * dr;
+    thr[b] = sq_threshold(c->rmin + bd, c->unit);
+  }
+  thr[c->nbins] = sq_threshold(c->rmax, c->unit);
+  CK(c, ensure(c, c->thr, thr.size() * 8));
+  CK(c, cudaMemcpyAsync(c->thr.p, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  return CTB_OK;
+}
+
+// float geometry of the grid and bins from c->unit, nc and g.shift
+void finish_geom(ctb_ctx* c, Geom& g, uint32_t nc) {
+  g.nc = nc;
+  g.ncells = nc * nc * nc;
+  const double rmin_u = c->rmin / c->unit, rmax_u = c->rmax / c->unit;
+  g.rlo2_u = (float)(rmin_u * rmin_u * (1.0 - 1e-5));
+  g.rhi2_u = (float)(rmax_u * rmax_u * (1.0 + 1e-5));
+  g.rmin_u = (float)rmin_u;
+  g.inv_dr_u = (float)(c->nbins / (rmax_u - rmin_u));
+  g.cell_scale = (float)(nc / std::ldexp(1.0, g.shift));
+  g.rcell = (float)(rmax_u * nc / std::ldexp(1.0, g.shift) * (1.0 + 1e-5) + 1e-3);
+}
+
 int bits_for(uint32_t ncells) {
   int b = 0;
   while (b < 32 && (1ull << b) < (unsigned long long)ncells) ++b;
@@ -293,6 +324,7 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   int r = ensure_events(c);
   if (r) return r;
   c->n = -1;
+  c->batch_keys = nullptr;
   const double* dxyz = xyz;
   const double* dw = w;
   if (n > 0 && !is_device_ptr(xyz)) {
@@ -363,32 +395,10 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
     double ncd = std::ceil(2147483648.0 * cpr / rmax_u);
     nc = (uint32_t)std::max(1.0, std::min(ncd, 1024.0));
   }
-  g.nc = nc;
-  g.ncells = nc * nc * nc;
-  const double rmin_u = c->rmin / c->unit, rmax_u = c->rmax / c->unit;
-  g.rlo2_u = (float)(rmin_u * rmin_u * (1.0 - 1e-5));
-  g.rhi2_u = (float)(rmax_u * rmax_u * (1.0 + 1e-5));
-  g.rmin_u = (float)rmin_u;
-  g.inv_dr_u = (float)(c->nbins / (rmax_u - rmin_u));
-  g.cell_scale = (float)(nc / std::ldexp(1.0, g.shift));
-  g.rcell = (float)(rmax_u * nc / std::ldexp(1.0, g.shift) * (1.0 + 1e-5) + 1e-3);
+  finish_geom(c, g, nc);
   c->g = g;
-
-  // exact edges, the same FP64 values an FP64 evaluation of the bins uses:
-  // r_min, r_min + b (r_max - r_min)/nbins, r_max
-  {
-    std::vector<unsigned long long> thr(c->nbins + 1);
-    const double dr = (c->rmax - c->rmin) / c->nbins;
-    thr[0] = sq_threshold(c->rmin, c->unit);
-    for (int b = 1; b < c->nbins; ++b) {
-      const double bd = b * dr;
-      thr[b] = sq_threshold(c->rmin + bd, c->unit);
-    }
-    thr[c->nbins] = sq_threshold(c->rmax, c->unit);
-    CK(c, ensure(c, c->thr, thr.size() * 8));
-    CK(c, cudaMemcpyAsync(c->thr.p, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice, c->st));
-    CK(c, cudaStreamSynchronize(c->st));
-  }
+  r = upload_thresholds(c);
+  if (r) return r;
 
   // buffers
   const size_t nn = (size_t)std::max<int64_t>(n, 1);
@@ -487,8 +497,55 @@ struct ChunkEv {
   cudaEvent_t e[6];
 };
 
+// Contraction of rows [off, off + cnt) of the current chunk's M into the
+// partials of segment `seg` (a catalogue of a batch; 0 otherwise).
+int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, size_t seg, cudaEvent_t* ev_pack) {
+  const int nb = c->nbins;
+  const size_t zsz = (size_t)(c->lmax + 1) * nb * nb;
+  const size_t rowsz = (size_t)nb * c->lay.row;
+  const float* M = P<float>(c->M) + (size_t)off * rowsz;
+  const float* wp = P<float>(c->wprim) + off;
+  if (c->precision != CTB_PREC_FP32) {
+    const bool tf32 = c->precision == CTB_PREC_TF32;
+    std::vector<unsigned long long> lb, kp;
+    size_t elems = 0;
+    tc_layout(tf32, cnt, nb, c->lmax, lb, kp, &elems);
+    const size_t esz = tf32 ? 4 : 2;
+    for (int k = 0; k < 4; ++k) {
+      if (tf32 && (k == 1 || k == 3)) continue;
+      CK(c, ensure(c, c->ops[k], elems * esz));
+      CK(c, cudaMemsetAsync(c->ops[k].p, 0, elems * esz, c->st));
+    }
+    CK(c, ensure(c, c->lbase_d, lb.size() * 8));
+    CK(c, ensure(c, c->kp_d, kp.size() * 8));
+    CK(c, cudaMemcpyAsync(c->lbase_d.p, lb.data(), lb.size() * 8, cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemcpyAsync(c->kp_d.p, kp.data(), kp.size() * 8, cudaMemcpyHostToDevice, c->st));
+    CK(c, launch_pack(tf32, M, wp, cnt, nb, c->lay.row, P<int>(c->slot_lm), P<unsigned long long>(c->lbase_d),
+                      P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p, c->ops[2].p, c->ops[3].p, c->st));
+    CK(c, cudaEventRecord(*ev_pack, c->st));
+    CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), c->ops[0].p, c->ops[1].p, c->ops[2].p,
+                             c->ops[3].p, P<double>(c->partial_tc) + seg * pl.nparts * zsz, pl.nparts,
+                             P<unsigned int>(c->flags) + 1, c->st));
+    // the host vectors lb / kp back the copies above: wait before releasing them
+    CK(c, cudaStreamSynchronize(c->st));
+  } else {
+    ContractArgs ca{};
+    ca.M = M;
+    ca.wprim = wp;
+    ca.np = cnt;
+    ca.nbins = nb;
+    ca.lmax = c->lmax;
+    ca.row = c->lay.row;
+    ca.slot = P<int>(c->slot);
+    ca.partial = P<double>(c->partial) + seg * pl.nparts * zsz;
+    ca.part0 = 0;
+    CK(c, launch_contract_fp32(ca, pl.nparts, c->st));
+  }
+  return CTB_OK;
+}
+
 int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, const PairPlan& pl,
-              float* alm_dev_out, uint64_t* npairs_out) {
+              float* alm_dev_out, uint64_t* npairs_out, const std::vector<int64_t>* seg_end = nullptr) {
   const int nb = c->nbins;
   CK(c, ensure(c, c->counts, (size_t)pl.chunk_max * nb * 4));
   CK(c, ensure(c, c->offsets, (size_t)pl.chunk_max * nb * 4));
@@ -508,6 +565,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   sa.wprim = P<float>(c->wprim);
   sa.work = work;
   sa.total = total;
+  sa.keys = c->batch_keys;
   sa.g = c->g;
   AlmArgs aa{};
   aa.pts = P<uint4>(c->pts);
@@ -559,42 +617,20 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     CK(c, cudaMemsetAsync(work, 0, 8, c->st));
     CK(c, launch_alm(aa, c->Lk, pl.wpb, pl.alm_blocks, c->st));
     CK(c, cudaEventRecord(ev[3], c->st));
-    if (contract && c->precision != CTB_PREC_FP32) {
-      const bool tf32 = c->precision == CTB_PREC_TF32;
-      std::vector<unsigned long long> lb, kp;
-      size_t elems = 0;
-      tc_layout(tf32, cnt, nb, c->lmax, lb, kp, &elems);
-      const size_t esz = tf32 ? 4 : 2;
-      for (int k = 0; k < 4; ++k) {
-        if (tf32 && (k == 1 || k == 3)) continue;
-        CK(c, ensure(c, c->ops[k], elems * esz));
-        CK(c, cudaMemsetAsync(c->ops[k].p, 0, elems * esz, c->st));
+    if (contract) {
+      // split the chunk at catalogue boundaries (a batch): each piece adds to its catalogue's partials
+      int64_t p0 = c0;
+      while (p0 < c0 + cnt) {
+        size_t seg = 0;
+        int64_t p1 = c0 + cnt;
+        if (seg_end) {
+          seg = (size_t)(std::upper_bound(seg_end->begin(), seg_end->end(), p0) - seg_end->begin());
+          p1 = std::min(p1, (*seg_end)[seg]);
+        }
+        int r = contract_piece(c, pl, p0 - c0, p1 - p0, seg, &ev[5]);
+        if (r) return r;
+        p0 = p1;
       }
-      CK(c, ensure(c, c->lbase_d, lb.size() * 8));
-      CK(c, ensure(c, c->kp_d, kp.size() * 8));
-      CK(c, cudaMemcpyAsync(c->lbase_d.p, lb.data(), lb.size() * 8, cudaMemcpyHostToDevice, c->st));
-      CK(c, cudaMemcpyAsync(c->kp_d.p, kp.data(), kp.size() * 8, cudaMemcpyHostToDevice, c->st));
-      CK(c, launch_pack(tf32, P<float>(c->M), P<float>(c->wprim), cnt, nb, c->lay.row, P<int>(c->slot_lm),
-                        P<unsigned long long>(c->lbase_d), P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p,
-                        c->ops[2].p, c->ops[3].p, c->st));
-      CK(c, cudaEventRecord(ev[5], c->st));
-      CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), c->ops[0].p, c->ops[1].p, c->ops[2].p,
-                               c->ops[3].p, P<double>(c->partial_tc), pl.nparts, P<unsigned int>(c->flags) + 1,
-                               c->st));
-      // host vectors lb / kp are read by the copies above before they are released
-      CK(c, cudaStreamSynchronize(c->st));
-    } else if (contract) {
-      ContractArgs ca{};
-      ca.M = P<float>(c->M);
-      ca.wprim = P<float>(c->wprim);
-      ca.np = cnt;
-      ca.nbins = nb;
-      ca.lmax = c->lmax;
-      ca.row = c->lay.row;
-      ca.slot = P<int>(c->slot);
-      ca.partial = P<double>(c->partial);
-      ca.part0 = 0;
-      CK(c, launch_contract_fp32(ca, pl.nparts, c->st));
     }
     if (alm_dev_out) {
       const int ncf = (c->lmax + 1) * (c->lmax + 1);
@@ -609,7 +645,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     CK(c, cudaEventSynchronize(ev[4]));
     t_stream += elapsed(ev[1], ev[2]);
     t_alm += elapsed(ev[2], ev[3]);
-    if (contract && c->precision != CTB_PREC_FP32) {
+    if (contract && c->precision != CTB_PREC_FP32 && !seg_end) {
       t_pack += elapsed(ev[3], ev[5]);
       t_con += elapsed(ev[5], ev[4]);
     } else {
@@ -650,7 +686,7 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
     CK(c, cudaMemsetAsync(c->partial_tc.p, 0, (size_t)pl.nparts * zsz * sizeof(double), c->st));
     CK(c, cudaMemsetAsync(P<unsigned int>(c->flags) + 1, 0, 4, c->st));
   }
-  for (int k = 0; k < kStages; ++k) c->t_ms[k] = 0;
+  for (int k = 2; k < kStages; ++k) c->t_ms[k] = 0;  // [0], [1]: the last ctb_set_points
   uint64_t pairs = 0;
   r = run_pairs(c, dprim, np, true, pl, nullptr, &pairs);
   if (r) return r;
@@ -669,6 +705,150 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
   CK(c, cudaStreamSynchronize(c->st));
   c->npairs = pairs;
   c->t_ms[5] = elapsed(c->ev[evs], c->ev[evs + 1]);
+  if (tc_err) return fail(c, CTB_ERR_TIMEOUT, "tensor-core contraction: a bounded wait timed out");
+  return CTB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch: k catalogues in one sorted grid (cell key = catalogue * cells + cell),
+// one chunked pair pipeline over all primaries, contraction pieces split at
+// catalogue boundaries into per-catalogue FP64 partials
+
+int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, const int64_t* n, int k,
+               double* zeta_out) {
+  if (k < 1 || !xyz || !n || !zeta_out) return fail(c, CTB_ERR_ARG, "batch: k < 1 or NULL argument");
+  if (!c->periodic) return fail(c, CTB_ERR_UNSUPPORTED, "batch mode needs a periodic box");
+  std::vector<int64_t> cum(k + 1, 0);
+  int64_t nmax = 0;
+  for (int i = 0; i < k; ++i) {
+    if (n[i] < 0) return fail(c, CTB_ERR_ARG, "batch: negative catalogue size");
+    if (n[i] > 0 && !xyz[i]) return fail(c, CTB_ERR_ARG, "batch: NULL xyz with n > 0");
+    cum[i + 1] = cum[i] + n[i];
+    nmax = std::max(nmax, n[i]);
+  }
+  const int64_t N = cum[k];
+  if (N >= (int64_t)1 << 31) return fail(c, CTB_ERR_ARG, "batch: more than 2^31 points in total");
+  CK(c, cudaSetDevice(c->dev));
+  int r = ensure_events(c);
+  if (r) return r;
+  r = ensure_tables(c);
+  if (r) return r;
+  c->n = -1;
+  c->batch_keys = nullptr;
+  // grid of one periodic catalogue
+  const int cpr = c->cells_per_rmax > 0 ? c->cells_per_rmax : 8;
+  Geom g{};
+  g.periodic = 1;
+  g.nbins = c->nbins;
+  g.lmax = c->lmax;
+  g.shift = 32;
+  c->unit = std::ldexp(c->box, -32);
+  const uint32_t nc = (uint32_t)std::max(1.0, std::min(std::floor(c->box * cpr / c->rmax), 1024.0));
+  finish_geom(c, g, nc);
+  c->g = g;
+  if ((uint64_t)k * g.ncells >= ((uint64_t)1 << 32) - 1)
+    return fail(c, CTB_ERR_ARG, "batch: catalogues x grid cells exceed 2^32 keys");
+  r = upload_thresholds(c);
+  if (r) return r;
+  const size_t nn = (size_t)std::max<int64_t>(N, 1);
+  CK(c, ensure(c, c->xyz_stage, nn * 3 * sizeof(double)));
+  CK(c, ensure(c, c->w_stage, nn * sizeof(double)));
+  CK(c, ensure(c, c->key0, nn * 4));
+  CK(c, ensure(c, c->val0, nn * 4));
+  CK(c, ensure(c, c->key1, nn * 4));
+  CK(c, ensure(c, c->val1, nn * 4));
+  CK(c, ensure(c, c->pts_in, nn * 16));
+  CK(c, ensure(c, c->pts, nn * 16));
+  CK(c, ensure(c, c->s2i, nn * 4));
+  CK(c, ensure(c, c->i2s, nn * 4));
+  const uint64_t cells_all = (uint64_t)k * g.ncells;
+  CK(c, ensure(c, c->cell_start, (size_t)(cells_all + 1) * 4));
+  const size_t hw = sort_hist_words(N);
+  CK(c, ensure(c, c->hist, hw * 4));
+  CK(c, ensure(c, c->scan_tmp, scan_tmp_words(hw) * 4));
+  CK(c, ensure(c, c->flags, 64));
+  CK(c, cudaMemsetAsync(c->flags.p, 0, 64, c->st));
+  CK(c, cudaEventRecord(c->ev[0], c->st));
+  for (int i = 0; i < k; ++i) {
+    if (n[i] == 0) continue;
+    const double* dx = xyz[i];
+    if (!is_device_ptr(dx)) {
+      CK(c, cudaMemcpyAsync(P<double>(c->xyz_stage) + 3 * cum[i], dx, (size_t)n[i] * 3 * sizeof(double),
+                            cudaMemcpyHostToDevice, c->st));
+      dx = P<double>(c->xyz_stage) + 3 * cum[i];
+    }
+    const double* dw = (w && w[i]) ? w[i] : nullptr;
+    if (dw && !is_device_ptr(dw)) {
+      CK(c, cudaMemcpyAsync(P<double>(c->w_stage) + cum[i], dw, (size_t)n[i] * sizeof(double),
+                            cudaMemcpyHostToDevice, c->st));
+      dw = P<double>(c->w_stage) + cum[i];
+    }
+    IngestOut io{P<uint32_t>(c->key0) + cum[i], P<uint32_t>(c->val0) + cum[i], P<uint4>(c->pts_in) + cum[i]};
+    CK(c, launch_ingest(dx, dw, n[i], c->box, nullptr, 1.0 / c->unit, g, io, P<uint32_t>(c->flags), c->st,
+                        (uint32_t)(i * g.ncells), (uint32_t)cum[i]));
+  }
+  CK(c, cudaEventRecord(c->ev[1], c->st));
+  SortBufs sb{P<uint32_t>(c->key0), P<uint32_t>(c->val0), P<uint32_t>(c->key1), P<uint32_t>(c->val1),
+              P<uint32_t>(c->hist), P<uint32_t>(c->scan_tmp)};
+  bool in1 = false;
+  int bits = 0;
+  while (bits < 32 && ((uint64_t)1 << bits) < cells_all) ++bits;
+  CK(c, radix_sort(sb, N, bits, &in1, c->st));
+  uint32_t* ks = in1 ? sb.k1 : sb.k0;
+  uint32_t* vs = in1 ? sb.v1 : sb.v0;
+  CK(c, launch_gather(vs, P<uint4>(c->pts_in), N, P<uint4>(c->pts), P<uint32_t>(c->s2i), P<uint32_t>(c->i2s), c->st));
+  CK(c, launch_cell_start(ks, N, (uint32_t)cells_all, P<uint32_t>(c->cell_start), c->st));
+  CK(c, cudaEventRecord(c->ev[2], c->st));
+  uint32_t fl = 0;
+  CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (fl) return fail(c, CTB_ERR_NONFINITE, "batch: non-finite coordinate or weight");
+  const double t_ingest = elapsed(c->ev[0], c->ev[1]), t_sort = elapsed(c->ev[1], c->ev[2]);
+  // pair pipeline over all primaries; densities planned from the largest catalogue
+  c->batch_keys = ks;
+  c->n = nmax;
+  PairPlan pl{};
+  r = plan_pairs(c, N, &pl);
+  c->n = -1;
+  if (r) {
+    c->batch_keys = nullptr;
+    return r;
+  }
+  const size_t zsz = (size_t)(c->lmax + 1) * c->nbins * c->nbins;
+  const size_t budget = (size_t)2 << 30;
+  pl.nparts = (int)std::max<size_t>(8, std::min<size_t>((size_t)pl.nparts, budget / ((size_t)k * zsz * 8)));
+  const bool tc = c->precision != CTB_PREC_FP32;
+  Buf& part = tc ? c->partial_tc : c->partial;
+  CK(c, ensure(c, part, (size_t)k * pl.nparts * zsz * sizeof(double)));
+  CK(c, cudaMemsetAsync(part.p, 0, (size_t)k * pl.nparts * zsz * sizeof(double), c->st));
+  if (tc) CK(c, cudaMemsetAsync(P<unsigned int>(c->flags) + 1, 0, 4, c->st));
+  CK(c, ensure(c, c->zeta, (size_t)k * zsz * sizeof(double)));
+  for (int i = 0; i < kStages; ++i) c->t_ms[i] = 0;
+  std::vector<int64_t> seg_end(cum.begin() + 1, cum.end());
+  uint64_t pairs = 0;
+  r = run_pairs(c, nullptr, N, true, pl, nullptr, &pairs, &seg_end);
+  c->batch_keys = nullptr;
+  if (r) return r;
+  CK(c, cudaEventRecord(c->ev[10], c->st));
+  for (int i = 0; i < k; ++i) {
+    const double* pi = P<double>(part) + (size_t)i * pl.nparts * zsz;
+    double* zi = P<double>(c->zeta) + (size_t)i * zsz;
+    if (tc)
+      CK(c, launch_finalize_tc(pi, c->lmax, pl.nparts, c->nbins, zi, c->st));
+    else
+      CK(c, launch_finalize(pi, pl.nparts, c->lmax, c->nbins, zi, c->st));
+  }
+  CK(c, cudaEventRecord(c->ev[11], c->st));
+  const bool dev_out = is_device_ptr(zeta_out);
+  CK(c, cudaMemcpyAsync(zeta_out, c->zeta.p, (size_t)k * zsz * sizeof(double),
+                        dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  unsigned int tc_err = 0;
+  if (tc) CK(c, cudaMemcpyAsync(&tc_err, P<unsigned int>(c->flags) + 1, 4, cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  c->npairs = pairs;
+  c->t_ms[0] = t_ingest;
+  c->t_ms[1] = t_sort;
+  c->t_ms[5] = elapsed(c->ev[10], c->ev[11]);
   if (tc_err) return fail(c, CTB_ERR_TIMEOUT, "tensor-core contraction: a bounded wait timed out");
   return CTB_OK;
 }
@@ -833,12 +1013,11 @@ int ctb_get_alm(ctb_ctx* c, const int64_t* primary_idx, int64_t m, float* alm_ou
 int ctb_compute_batch(ctb_ctx* c, const double* const* xyz, const double* const* w, const int64_t* n, int k,
                       double* zeta_out) {
   if (!c) return CTB_ERR_ARG;
-  return fail(c, CTB_ERR_UNSUPPORTED, "batch mode not available in this build");
-  (void)xyz;
-  (void)w;
-  (void)n;
-  (void)k;
-  (void)zeta_out;
+  const unsigned long long l0 = g_launches;
+  int r = batch_impl(c, xyz, w, n, k, zeta_out);
+  c->launches_points = 0;
+  c->launches_compute = g_launches - l0;
+  return r;
 }
 
 int ctb_set_option(ctb_ctx* c, int key, int64_t v) {

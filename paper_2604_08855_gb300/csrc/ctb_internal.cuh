@@ -132,10 +132,13 @@ struct IngestOut {
   uint32_t* val;    // input index
   uint4* pts;       // fixed-point point per input index
 };
-// box > 0: periodic; else origin/inv_unit map into [0, 2^31)
+// box > 0: periodic; else origin/inv_unit map into [0, 2^31).  key_base is
+// added to every cell key (catalogue index * cells per catalogue in a batch),
+// val_base to every input index.
 cudaError_t launch_ingest(const double* xyz, const double* w, int64_t n, double box,
                           const double* origin3, double inv_unit, const Geom& g,
-                          IngestOut out, uint32_t* d_flags, cudaStream_t st);
+                          IngestOut out, uint32_t* d_flags, cudaStream_t st,
+                          uint32_t key_base = 0, uint32_t val_base = 0);
 cudaError_t launch_bbox(const double* xyz, int64_t n, double* d_part, int nblk,
                         uint32_t* d_flags, cudaStream_t st);
 int bbox_blocks(int64_t n);
@@ -173,6 +176,7 @@ struct StreamArgs {
   float* wprim;                   // [prim_count] primary weights                      (count pass)
   unsigned long long* work;       // work counter (zeroed before launch)
   unsigned long long* total;      // binned pairs of this launch (count pass, accumulated)
+  const uint32_t* keys;           // sorted cell keys of a batch (catalogue = key / ncells), or NULL
   Geom g;
 };
 int stream_blocks_per_sm(bool fill, int nbins);

@@ -15,8 +15,8 @@ namespace ctb {
 
 __global__ void k_ingest(const double* __restrict__ xyz, const double* __restrict__ w, int64_t n,
                          double box, double ox, double oy, double oz, double inv_unit, Geom g,
-                         uint32_t* __restrict__ key, uint32_t* __restrict__ val, uint4* __restrict__ pts,
-                         uint32_t* flags) {
+                         uint32_t key_base, uint32_t val_base, uint32_t* __restrict__ key,
+                         uint32_t* __restrict__ val, uint4* __restrict__ pts, uint32_t* flags) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double p[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
@@ -46,22 +46,22 @@ __global__ void k_ingest(const double* __restrict__ xyz, const double* __restric
       u[k] = (uint32_t)s;
       c[k] = (uint32_t)(((uint64_t)u[k] * g.nc) >> g.shift);
     }
-    key[i] = (c[2] * g.nc + c[1]) * g.nc + c[0];
-    val[i] = (uint32_t)i;
+    key[i] = key_base + (c[2] * g.nc + c[1]) * g.nc + c[0];
+    val[i] = val_base + (uint32_t)i;
     pts[i] = make_uint4(u[0], u[1], u[2], __float_as_uint((float)wi));
   }
 }
 
 cudaError_t launch_ingest(const double* xyz, const double* w, int64_t n, double box,
                           const double* origin3, double inv_unit, const Geom& g, IngestOut out,
-                          uint32_t* d_flags, cudaStream_t st) {
+                          uint32_t* d_flags, cudaStream_t st, uint32_t key_base, uint32_t val_base) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 65535 * 4) blocks = 65535 * 4;
   double o[3] = {0, 0, 0};
   if (origin3) { o[0] = origin3[0]; o[1] = origin3[1]; o[2] = origin3[2]; }
-  k_ingest<<<blocks, 256, 0, st>>>(xyz, w, n, box, o[0], o[1], o[2], inv_unit, g, out.key,
-                                   out.val, out.pts, d_flags);
+  k_ingest<<<blocks, 256, 0, st>>>(xyz, w, n, box, o[0], o[1], o[2], inv_unit, g, key_base, val_base,
+                                   out.key, out.val, out.pts, d_flags);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -62,6 +62,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
     const int64_t gi = a.prim_begin + (int64_t)i;
     const uint32_t sp = a.prim ? __ldg(a.prim + gi) : (uint32_t)gi;
     const uint4 P = __ldg(a.pts + sp);
+    // batch: the primary's catalogue owns cells [cat * ncells, (cat + 1) * ncells)
+    const uint32_t cbase = a.keys ? (__ldg(a.keys + sp) / g.ncells) * g.ncells : 0u;
     if (!FILL && lane == 0) a.wprim[i] = __uint_as_float(P.w);
     const uint64_t ib = i * (uint64_t)nbins;
     if (FILL) {
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
         if (ok) {
           const float hw = sqrtf(R2 - rho2);
           int lo = (int)floorf(fx - hw), hi = (int)floorf(fx + hw);
-          const uint32_t rb = ((uint32_t)cz * nc + (uint32_t)cy) * nc;
+          const uint32_t rb = cbase + ((uint32_t)cz * nc + (uint32_t)cy) * nc;
           int a0 = 1, b0 = 0, a1 = 1, b1 = 0;
           if (g.periodic) {
             if (hi - lo + 1 >= (int)nc) {

@@ -253,3 +253,82 @@ def test_tensor_core_chunks_and_negative_weights(ctbmod):
     z, _ = run_full(ctbmod, xyz, w, kw, precision=ctbmod.PREC_BF16X3, chunk_primaries=1024)
     ref = oracle.zeta(xyz, w, **kw)
     assert zeta_err(z, ref) < TOL_MIXED
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["FP32", "BF16X3"])
+def test_thomas_4m_subset_200k_full_vs_oracle(ctbmod, prec):
+    """The seeded 200k subset of the 4M Thomas catalogue (L = 2000, r in
+    [10, 200], 32 bins, l_max 20): full zeta against the oracle."""
+    xyz, w = synth.thomas_4m_subset()
+    kw = synth.config_params(3)
+    z, est = run_full(ctbmod, xyz, w, kw, precision=getattr(ctbmod, "PREC_" + prec))
+    ref = _cached_oracle("thomas_4m_subset", xyz, w, kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < (TOL_FP32 if prec == "FP32" else TOL_MIXED)
+
+
+@pytest.mark.slow
+def test_cut_sky_sampled_primaries(ctbmod):
+    """Cut-sky sector: 8M clustered data (w = +1) and 24M uniform randoms
+    (w = -1/3), open boundary, r in [20, 200], 36 bins, l_max 10; 192 seeded
+    primaries with all 32M secondaries, against the oracle."""
+    xyz, w = synth.cut_sky()
+    kw = synth.config_params(5)
+    est = make(ctbmod, **kw)
+    est.set_points(xyz, w)
+    prim = synth.sample_primaries(xyz.shape[0], 192, seed=7)
+    z = est.compute_subset(prim)
+    ref = oracle.zeta(xyz, w, prim=prim, **kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < TOL_FP32
+
+
+_ORACLE_CACHE = {}
+
+
+def _cached_oracle(key, xyz, w, kw):
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = oracle.zeta(xyz, w, **kw)
+    return _ORACLE_CACHE[key]
+
+
+# ------------------------------------------------------------------ batches
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16X3"])
+def test_batch_matches_single_catalogues(ctbmod, prec):
+    """Uneven mock catalogues (one empty) in one batch: each zeta matches the
+    catalogue computed alone, and two of them match the oracle."""
+    sizes = [3000, 0, 700, 5200, 1500]
+    cats = [synth.thomas(n, 300.0, max(1, n // 100), 5.0, seed=60 + i, weights="u0.5-1.5") for i, n in
+            enumerate(sizes)]
+    kw = dict(box=300.0, rmin=2.0, rmax=40.0, nbins=6, lmax=8)
+    opts = dict(precision=getattr(ctbmod, "PREC_" + prec))
+    est = make(ctbmod, **kw, **opts)
+    zb = est.compute_batch(cats)
+    assert zb.shape == (len(sizes), 9, 6, 6)
+    assert np.all(zb[1] == 0)
+    tol = TOL_FP32 if prec == "FP32" else TOL_MIXED
+    for i, (xyz, w) in enumerate(cats):
+        if sizes[i] == 0:
+            continue
+        zs, _ = run_full(ctbmod, xyz, w, kw, **opts)
+        ref = oracle.zeta(xyz, w, **kw) if i in (2, 3) else None
+        if ref is not None:
+            assert zeta_err(zb[i], ref) < tol
+            assert zeta_err(zs, ref) < tol
+        scale = np.abs(zs).max()
+        assert np.max(np.abs(zb[i] - zs)) <= 1e-6 * scale
+    # the batch replaced the context's catalogue
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.compute()
+    assert e.value.code == ctbmod.ERR_STATE
+
+
+def test_batch_rejects_open_boundary(ctbmod):
+    est = make(ctbmod, box=0.0, rmin=1.0, rmax=10.0, nbins=2, lmax=2)
+    xyz, w = synth.uniform(100, 50.0, seed=1)
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.compute_batch([(xyz, w)])
+    assert e.value.code == ctbmod.ERR_UNSUPPORTED
