@@ -38,6 +38,13 @@ METRIC = "pair-multipole updates/s (zeta_ell 3PCF, 1 GB300)"
 UNIT = "updates/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
+# Algorithmic work of the accumulation step per (pair, coefficient) update:
+# about one FMA to accumulate plus the recurrence share, in FP32 instructions.
+INST_PER_UPDATE = 2.6
+# DRAM bytes per pair of the accumulation kernel from one ncu capture of the
+# current k_alm (dram__bytes_read.sum + dram__bytes_write.sum over the pairs of
+# the captured launch); None when the kernel changed after the capture.
+K_ALM_DRAM_BYTES_PER_PAIR = None
 FP32_LANES_PER_SM = 128
 
 
@@ -110,6 +117,15 @@ def flops_per_pair(lmax: int) -> int:
                     f += 2 + (4 if m + 1 <= L else 0) + 7 * max(0, L - m - 1)
         m0 = m1 + 1
     return f
+
+
+def traffic_per_launch(npairs: int, chunks: int):
+    """DRAM bytes of one mean k_alm launch of this run, scaled from the
+    captured launch by its pairs (the traffic is the list words, which grow
+    with the pairs), or None."""
+    if K_ALM_DRAM_BYTES_PER_PAIR is None or chunks <= 0:
+        return None
+    return K_ALM_DRAM_BYTES_PER_PAIR * npairs / chunks
 
 
 def peaks():
@@ -326,6 +342,7 @@ def run_ours(args):
             stages.append(tm)
             launches += est.launch_count()
             npairs = est.pair_count()
+            chunks = est.chunk_count()
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - wall0
     barrier(world)
@@ -352,9 +369,13 @@ def run_ours(args):
 
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # FP32 lane-instruction peak (one FMA-pipe instruction per lane per clock)
+    peak_tinst = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     pair_s = float(np.mean(pair_ms)) / 1e3
-    achieved = npairs * flops_per_pair(kw["lmax"]) / pair_s / 1e12
+    # algorithmic work of the accumulation: INST_PER_UPDATE FP32 instructions
+    # per (pair, coefficient) update, over the kernel's own event time
+    achieved = npairs * nc * INST_PER_UPDATE / pair_s / 1e12
+    impl_tflops = npairs * flops_per_pair(kw["lmax"]) / pair_s / 1e12
     st = np.mean(np.array(stages), axis=0)
     names = ["ingest", "sort_grid", "pair_total", "pack", "contraction", "reduce", "enumerate", "accumulate"]
     stages_ms = {k: round(float(v), 3) for k, v in zip(names, st)}
@@ -367,13 +388,17 @@ def run_ours(args):
                    "inputs": "device-resident float64 xyz, w"},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_alm", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
-                     "peak_note": f"FP32 FMA pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+        "roofline": {"bound": "alu", "kernel": "k_alm", "achieved": achieved, "peak": peak_tinst,
+                     "unit": "Tinst/s", "frac": achieved / peak_tinst, "traffic": traffic_per_launch(npairs, chunks),
+                     "launches_per_step": chunks,
+                     "work_per_unit": f"{INST_PER_UPDATE} FP32 instructions per update",
+                     "peak_note": f"FP32 pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
                                   f"{sm_max:.0f} MHz ({pk_kind} max clock)",
-                     "flops_per_pair": flops_per_pair(kw["lmax"]), "kernel_ms": 1e3 * pair_s},
+                     "impl_flops_per_pair": flops_per_pair(kw["lmax"]), "impl_tflops": impl_tflops,
+                     "impl_frac": impl_tflops / (2 * peak_tinst), "kernel_ms": 1e3 * pair_s},
         "stages_ms": stages_ms,
         "pairs_per_step": npairs,
+        "pairs_per_s": world * args.steps * npairs / t_total,
         "ms_per_zeta_ell": ms_per_step / (kw["lmax"] + 1),
         "wall_s": wall,
         "clocks": clocks,

@@ -191,6 +191,12 @@ int ctb_get_launch_count(ctb_ctx* ctx, uint64_t* kernels);
 /* Number of ordered (primary, secondary) pairs binned by the last compute. */
 int ctb_get_pair_count(ctb_ctx* ctx, uint64_t* pairs);
 
+/* Number of primary chunks the last compute ran.  Each chunk is one launch of
+ * each pair kernel (count, fill, accumulate) over its own neighbour lists, so
+ * pairs / chunks is the mean work of one launch.  A chunk that overflowed the
+ * list buffer and was split is not counted.  0 before the first compute. */
+int ctb_get_chunk_count(ctb_ctx* ctx, uint64_t* chunks);
+
 /*
  * zeta_l(b1,b2) from a_lm rows and primary weights already on the device,
  * without allocating any device memory.  The paper has no counterpart: this

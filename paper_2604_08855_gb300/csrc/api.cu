@@ -66,6 +66,7 @@ struct ctb_ctx {
   bool ev_ready = false;
   double t_ms[kStages] = {0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t npairs = 0;
+  uint64_t nchunks = 0;  // primary chunks of the last compute
   unsigned long long launches_points = 0, launches_compute = 0;
 };
 
@@ -581,7 +582,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   aa.row = c->lay.row;
   std::memcpy(aa.beta, c->beta, sizeof(aa.beta));
   double t_stream = 0, t_alm = 0, t_con = 0, t_pack = 0;
-  uint64_t pairs = 0;
+  uint64_t pairs = 0, chunks = 0;
   int64_t C = pl.chunk_first;
   int64_t c0 = 0;
   // [0] count start [1] count end [2] fill end [3] alm end [4] contraction end [5] pack end
@@ -652,6 +653,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
       t_con += elapsed(ev[3], ev[4]);
     }
     pairs += tot;
+    ++chunks;
     c0 += cnt;
     // next chunk: fill about 90 % of the list buffer at the observed density
     const double per = cnt > 0 ? (double)tot / (double)cnt : 0.0;
@@ -663,6 +665,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   c->t_ms[4] = t_con;
   c->t_ms[6] = t_stream;
   c->t_ms[7] = t_alm;
+  c->nchunks = chunks;
   *npairs_out = pairs;
   return CTB_OK;
 }
@@ -1089,6 +1092,12 @@ int ctb_get_launch_count(ctb_ctx* c, uint64_t* kernels) {
 int ctb_get_pair_count(ctb_ctx* c, uint64_t* pairs) {
   if (!c || !pairs) return CTB_ERR_ARG;
   *pairs = c->npairs;
+  return CTB_OK;
+}
+
+int ctb_get_chunk_count(ctb_ctx* c, uint64_t* chunks) {
+  if (!c || !chunks) return CTB_ERR_ARG;
+  *chunks = c->nchunks;
   return CTB_OK;
 }
 

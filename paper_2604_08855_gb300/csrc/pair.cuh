@@ -30,6 +30,13 @@
 namespace ctb {
 
 constexpr uint32_t kNone = 0xffffffffu;
+// The list words of one primary are one contiguous range; the read position
+// is kept this many 128-byte lines ahead of use in L2.
+constexpr uint32_t kListPrefetchLines = 6;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // Columns accumulated as Chebyshev moments: m <= cheb_max_m(L).  Above it
 // the monic Legendre recurrence is used (its conditioning does not degrade
@@ -219,7 +226,7 @@ __device__ __forceinline__ Prefetch prefetch_start(const uint32_t* lists, const 
 // next run starts without a memory bubble.
 template <int L, int M0, int M1>
 __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, const uint4 P, Prefetch& pf,
-                                         float* __restrict__ out, int base, float* sbuf, int lane) {
+                                         float* __restrict__ out, int base, float* sbuf, int lane, uint32_t pe) {
   constexpr int NCP = round32(coef_count(L, M0, M1));
   const uint32_t* __restrict__ lists = a.lists;
   const uint4* __restrict__ pts = a.pts;
@@ -231,6 +238,8 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
   // when it is a single step long, so take it from (cur, nxt)
   pf.j1 = rec_at(lists, cur, nxt, T, 1, lane);
   for (uint32_t t = 0; t < T; ++t) {
+    const uint32_t pa = cur.off + (t + kListPrefetchLines) * 32u;
+    if (lane == 0 && pa < pe) prefetch_l2(lists + pa);
     const uint4 q = pf.q0;
     const bool valid = pf.j0 != kNone;
     pf.j0 = pf.j1;
@@ -283,9 +292,9 @@ struct PassChain {
   static constexpr int NCP = round32(coef_count(L, M0, M1));
   static constexpr bool LAST = M1 + 1 > L;
   __device__ static __forceinline__ void run(const AlmArgs& a, Run cur, Run nxt_bin, const uint4 P, Prefetch& pf,
-                                             float* out, float* sbuf, int lane) {
-    run_pass<L, M0, M1>(a, cur, LAST ? nxt_bin : cur, P, pf, out + BASE, BASE, sbuf, lane);
-    if constexpr (!LAST) PassChain<L, M1 + 1, BASE + NCP>::run(a, cur, nxt_bin, P, pf, out, sbuf, lane);
+                                             float* out, float* sbuf, int lane, uint32_t pe) {
+    run_pass<L, M0, M1>(a, cur, LAST ? nxt_bin : cur, P, pf, out + BASE, BASE, sbuf, lane, pe);
+    if constexpr (!LAST) PassChain<L, M1 + 1, BASE + NCP>::run(a, cur, nxt_bin, P, pf, out, sbuf, lane, pe);
   }
 };
 
@@ -346,10 +355,14 @@ __global__ void __launch_bounds__(128, 3) k_alm(AlmArgs a) {
       while (nb < nbins && s_n[nb] == 0) ++nb;
       Run cur{s_off[b], s_n[b]};
       Run nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
+      // end of this primary's list range; its first lines go to L2 now
+      const uint32_t pe = s_off[nbins - 1] + s_n[nbins - 1];
+      if (lane < (int)kListPrefetchLines && cur.off + (uint32_t)lane * 32u < pe)
+        prefetch_l2(a.lists + cur.off + (uint32_t)lane * 32u);
       // the first pass continues into the same bin when more m-passes follow
       Prefetch pf = prefetch_start(a.lists, a.pts, cur, PassChain<L, 0, 0>::LAST ? nxt : cur, P, lane);
       while (true) {
-        PassChain<L, 0, 0>::run(a, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, sbuf, lane);
+        PassChain<L, 0, 0>::run(a, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, sbuf, lane, pe);
         b = nb;
         if (b >= nbins) break;
         cur = nxt;

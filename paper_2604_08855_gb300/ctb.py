@@ -30,7 +30,7 @@ LMAX_CAP, NBINS_CAP = 20, 64
 # every symbol include/ctb.h declares
 EXPORTS = ("ctb_create", "ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm",
            "ctb_compute_batch", "ctb_set_option", "ctb_set_stream", "ctb_set_allocator",
-           "ctb_get_timings", "ctb_get_pair_count", "ctb_get_launch_count", "ctb_contract_noalloc",
+           "ctb_get_timings", "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_launch_count", "ctb_contract_noalloc",
            "ctb_destroy", "ctb_last_error", "ctb_version")
 
 _lib = None
@@ -64,6 +64,7 @@ def load(path: str | None = None):
     lib.ctb_set_allocator.argtypes = [vp, vp, vp, vp]
     lib.ctb_get_timings.argtypes = [vp, vp, i32]
     lib.ctb_get_pair_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.ctb_get_chunk_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.ctb_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.ctb_contract_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     lib.ctb_destroy.argtypes = [vp]
@@ -74,7 +75,7 @@ def load(path: str | None = None):
     lib.ctb_version.restype = ctypes.c_char_p
     for name in ("ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm", "ctb_compute_batch",
                  "ctb_set_option", "ctb_set_stream", "ctb_set_allocator", "ctb_get_timings",
-                 "ctb_get_pair_count", "ctb_get_launch_count", "ctb_contract_noalloc"):
+                 "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_launch_count", "ctb_contract_noalloc"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -229,6 +230,12 @@ class CTB:
     def pair_count(self) -> int:
         v = ctypes.c_uint64(0)
         self._check(self.lib.ctb_get_pair_count(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def chunk_count(self) -> int:
+        """Primary chunks (launches of each pair kernel) of the last compute."""
+        v = ctypes.c_uint64(0)
+        self._check(self.lib.ctb_get_chunk_count(self._h, ctypes.byref(v)))
         return int(v.value)
 
 

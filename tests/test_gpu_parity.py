@@ -250,7 +250,8 @@ def test_tensor_core_chunks_and_negative_weights(ctbmod):
     xyz, _ = synth.uniform(6000, 250.0, seed=29)
     w = np.random.default_rng(29).uniform(-1.0, 1.0, xyz.shape[0])
     kw = dict(box=250.0, rmin=2.0, rmax=40.0, nbins=6, lmax=6)
-    z, _ = run_full(ctbmod, xyz, w, kw, precision=ctbmod.PREC_BF16X3, chunk_primaries=1024)
+    z, est = run_full(ctbmod, xyz, w, kw, precision=ctbmod.PREC_BF16X3, chunk_primaries=1024)
+    assert est.chunk_count() == 6  # 6000 primaries in chunks of at most 1024
     ref = oracle.zeta(xyz, w, **kw)
     assert zeta_err(z, ref) < TOL_MIXED
 
