@@ -13,5 +13,9 @@ Parity status of each function (what pins it is listed in the tests):
   zeta   pinned: O(N^3) triplet sum with numpy Legendre polynomials, the
          l = 0 closed form with scipy's cKDTree neighbour counts, hand-built
          geometries with printed P_l values, invariances.
+  edge.edge_correct  pinned: sympy's Wigner 3j symbols, exact Legendre
+         quotients built with numpy's legmul, flat randoms (plain ratio),
+         quadrature of N/R.
 """
 from .oracle import build, ylm, alm, zeta, max_threads, lib_path  # noqa: F401
+from . import edge  # noqa: F401
