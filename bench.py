@@ -303,6 +303,10 @@ def run_ours(args):
     est.set_stream(stream)
     if args.precision != "fp32":
         est.set_option(ctb.OPT_PRECISION, {"bf16x3": ctb.PREC_BF16X3, "tf32": ctb.PREC_TF32}[args.precision])
+    if args.cells_per_rmax:
+        est.set_option(ctb.OPT_CELLS_PER_RMAX, args.cells_per_rmax)
+    else:
+        est.set_option(ctb.OPT_AUTOTUNE, 1)  # tuned on the first set_points (a warm-up step)
     d_xyz = torch.from_numpy(xyz).to(dev)
     d_w = torch.from_numpy(w).to(dev)
     d_zeta = torch.zeros(est.zeta_shape, dtype=torch.float64, device=dev)
@@ -384,7 +388,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**cfg, "precision": args.precision, "l2": "flushed (256 MB write) before every step",
+        "config": {**cfg, "precision": args.precision, "cells_per_rmax": est.grid()[0],
+                   "grid": "fixed" if args.cells_per_rmax else "autotuned",
+                   "l2": "flushed (256 MB write) before every step",
                    "inputs": "device-resident float64 xyz, w"},
         "e2e": e2e,
         "gpu_launches": launches,
@@ -426,6 +432,8 @@ def main():
     ap.add_argument("--primaries", type=int, default=0,
                     help="profiling case: time ctb_compute_subset over this many seeded primaries")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cells-per-rmax", type=int, default=0,
+                    help="grid cells per r_max (0: the library's autotuner picks)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -65,10 +65,20 @@ typedef struct ctb_ctx ctb_ctx;
 /* option keys for ctb_set_option */
 #define CTB_OPT_PRECISION 1      /* contraction precision, CTB_PREC_* (default FP32)        */
 #define CTB_OPT_CELLS_PER_RMAX 2 /* grid cells per r_max along an axis, 1..64 (0 = auto)    */
-#define CTB_OPT_BIN_CAPACITY 3   /* per-warp neighbour-list capacity per bin, 256..65536    */
+#define CTB_OPT_LIST_CAPACITY 3  /* neighbour-list entries per chunk, 4096..2^32 (0 = 2^32) */
 #define CTB_OPT_WARPS_PER_BLOCK 4/* pair-kernel warps per block, 1..16 (0 = auto)           */
 #define CTB_OPT_CHUNK_PRIMARIES 5/* primaries per pair-kernel launch, >= 1024 (0 = auto)    */
 #define CTB_OPT_DETERMINISTIC 6  /* 1: fixed reduction order (default 1)                    */
+#define CTB_OPT_AUTOTUNE 7       /* 1: time the grid cell sizes on the next set_points    */
+#define CTB_OPT_FAULT_INJECT 8   /* test hook: 0 none, CTB_INJECT_STALL, CTB_INJECT_ALLOC   */
+
+/* injected faults (CTB_OPT_FAULT_INJECT); nothing faults, traps or hangs the GPU */
+#define CTB_INJECT_STALL 1 /* the tensor-core contraction's MMA thread first waits on a
+                              barrier nothing signals; the wait gives up after ~10 ms, the
+                              kernel takes its abort path, compute returns CTB_ERR_TIMEOUT
+                              and the context stays usable */
+#define CTB_INJECT_ALLOC 2 /* every device allocation the context attempts fails:
+                              CTB_ERR_OOM */
 
 /* contraction precisions (zeta = M^T W M per ell on the tensor cores or not) */
 #define CTB_PREC_FP32 0   /* plain FP32 on the CUDA cores                       */
@@ -155,7 +165,17 @@ int ctb_compute_batch(ctb_ctx* ctx, const double* const* xyz, const double* cons
                       const int64_t* n, int k, double* zeta_out);
 
 /* Set an option (CTB_OPT_*).  Returns CTB_ERR_ARG for an unknown key or a value
- * out of range, CTB_ERR_UNSUPPORTED for a precision this build cannot run. */
+ * out of range, CTB_ERR_UNSUPPORTED for a precision this build cannot run.
+ * CTB_OPT_LIST_CAPACITY bounds the neighbour lists of one chunk of primaries
+ * (4 bytes per entry) and the candidates' bin codes of that chunk (1 byte per
+ * candidate, at most 4 per list entry of the capacity); chunks are sized to
+ * fit, and a compute in which one primary alone has more pairs (or candidates)
+ * than that fails with CTB_ERR_OOM.
+ * CTB_OPT_AUTOTUNE = 1 (with CTB_OPT_CELLS_PER_RMAX left at 0) makes the next
+ * ctb_set_points grid the catalogue at 3, 4, 6, 8, 12 and 16 cells per r_max,
+ * time the pair kernels on a sample of at most 8192 primaries for each, and
+ * keep the fastest grid for this context (setting the option again re-tunes).
+ * The result does not depend on the grid beyond FP32 summation order. */
 int ctb_set_option(ctb_ctx* ctx, int key, int64_t value);
 
 /* Issue all further work on `stream` (a cudaStream_t of the context's device,
@@ -196,6 +216,43 @@ int ctb_get_pair_count(ctb_ctx* ctx, uint64_t* pairs);
  * pairs / chunks is the mean work of one launch.  A chunk that overflowed the
  * list buffer and was split is not counted.  0 before the first compute. */
 int ctb_get_chunk_count(ctb_ctx* ctx, uint64_t* chunks);
+
+/*
+ * Two-point function from the same pass (paper, "Statement of need": the
+ * 2PCF alongside the 3PCF).  out[k * nbins + b] = sum_p w_p sum_{j != p,
+ * r_pj in bin b} w_j, the weighted pair sums of the last ctb_compute /
+ * ctb_compute_subset (k = 0; over the given primaries) or of each catalogue k
+ * of the last ctb_compute_batch.  They come from the a_00 column of the
+ * accumulation (a_00 = sum_j w_j / sqrt(4 pi)), FP32 per (primary, bin) and
+ * FP64 over primaries.  `cap` is the capacity of the host array `out`.
+ * Returns the number of values written (catalogues * nbins), CTB_ERR_STATE if
+ * no zeta was computed since the last ctb_set_points, CTB_ERR_ARG if cap is
+ * too small.
+ */
+int ctb_get_2pcf(ctb_ctx* ctx, double* out, int cap);
+
+/*
+ * Edge-corrected multipoles (Slepian & Eisenstein 2015; paper, "Implementation":
+ * edge corrections).  Inputs are two results of ctb_compute with this
+ * context's ell_max and nbins, [(ell_max+1)][nbins][nbins] FP64:
+ *   zeta_nnn  the data-minus-randoms catalogue (randoms with negative weights)
+ *   zeta_rrr  the randoms alone, with the same weights taken positive
+ * Per bin pair the coefficients zeta_l of zeta(mu) = N(mu) / R(mu) =
+ * sum_l zeta_l P_l(mu) solve  n_l / r_0 = sum_l' M_ll' zeta_l'  with
+ *   n_l = (2l+1)/2 zeta_nnn_l,  r_l = (2l+1)/2 zeta_rrr_l,  f_l = r_l / r_0,
+ *   M_ll' = (2l+1) sum_l'' (l l' l''; 0 0 0)^2 f_l''   (all l <= ell_max),
+ * in FP64 on the device (one thread per bin pair, partial pivoting).
+ * zeta_out receives zeta_l [(ell_max+1)][nbins][nbins]; bin pairs without
+ * random triplets or with a singular system are NaN.  Pointers may be host
+ * or device memory; the caller keeps them.  Returns CTB_OK, CTB_ERR_ARG,
+ * CTB_ERR_OOM or CTB_ERR_CUDA.
+ */
+int ctb_edge_correct(ctb_ctx* ctx, const double* zeta_nnn, const double* zeta_rrr, double* zeta_out);
+
+/* The cell grid of the current catalogue: cells per r_max along an axis (the
+ * option, else the autotuner's choice, else 8) and cells per axis of the
+ * (per-catalogue) cube.  CTB_ERR_STATE before ctb_set_points. */
+int ctb_get_grid(ctb_ctx* ctx, int* cells_per_rmax, int* cells_per_axis);
 
 /*
  * zeta_l(b1,b2) from a_lm rows and primary weights already on the device,

@@ -36,7 +36,9 @@ struct ctb_ctx {
   // options
   int precision = CTB_PREC_FP32;
   int cells_per_rmax = 0;
-  uint32_t cap = 1024;
+  int autotune = 0;
+  int inject = 0;     // CTB_INJECT_* test hook
+  int tuned_cpr = 0;  // cells per r_max chosen by the autotuner (0: none yet)
   int wpb = 0;
   int64_t chunk = 0;
   int deterministic = 1;
@@ -58,6 +60,11 @@ struct ctb_ctx {
   // device buffers
   Buf xyz_stage, w_stage, key0, val0, key1, val1, hist, scan_tmp, pts_in, pts, s2i, i2s, cell_start;
   Buf flags, bbox_part, lists, M, wprim, partial, zeta, prim, counters, norm, slot, idx64, alm, thr;
+  Buf edge_in, edge_tj;  // edge correction: staged sums, 3j table
+  Buf pairsum;          // FP64 partial pair sums [catalogue][part][bin] of the last compute
+  int pairsum_segs = 0;  // catalogues they cover (0: none)
+  int pairsum_parts = 0;
+  Buf codes, code_base;  // per-candidate bin codes of a chunk; range start per (primary, row block)
   Buf counts, offsets, scan_tmp2;
   Buf ops[4], slot_lm, lbase_d, kp_d, partial_tc, conv_off, conv_src, conv_coef;
   uint64_t list_cap = (uint64_t)1 << 32;  // neighbour-list entries per chunk (16 GB)
@@ -103,6 +110,7 @@ void release(ctb_ctx* c, Buf& b) {
 cudaError_t ensure(ctb_ctx* c, Buf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return cudaSuccess;
+  if (c->inject == CTB_INJECT_ALLOC) return cudaErrorMemoryAllocation;
   release(c, b);
   size_t want = (bytes + 255) & ~(size_t)255;
   void* p = nullptr;
@@ -137,7 +145,7 @@ void release_all(ctb_ctx* c) {
   Buf* all[] = {&c->xyz_stage, &c->w_stage, &c->key0, &c->val0, &c->key1, &c->val1, &c->hist,
                 &c->scan_tmp, &c->pts_in, &c->pts, &c->s2i, &c->i2s, &c->cell_start, &c->flags,
                 &c->bbox_part, &c->lists, &c->M, &c->wprim, &c->partial, &c->zeta, &c->prim,
-                &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr, &c->counts,
+                &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr, &c->codes, &c->code_base, &c->pairsum, &c->edge_in, &c->edge_tj, &c->counts,
                 &c->offsets, &c->scan_tmp2, &c->ops[0], &c->ops[1], &c->ops[2], &c->ops[3],
                 &c->slot_lm, &c->lbase_d, &c->kp_d, &c->partial_tc, &c->conv_off, &c->conv_src,
                 &c->conv_coef};
@@ -318,6 +326,13 @@ int bits_for(uint32_t ncells) {
 // ---------------------------------------------------------------------------
 // catalogue load: ingest -> radix sort by cell -> gather -> cell table
 
+// Cells per r_max along an axis: the option if set, else the autotuner's
+// choice, else 8.
+int grid_cells_per_rmax(const ctb_ctx* c) {
+  if (c->cells_per_rmax > 0) return c->cells_per_rmax;
+  return c->tuned_cpr > 0 ? c->tuned_cpr : 8;
+}
+
 int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   if (n < 0 || n >= (int64_t)1 << 31) return fail(c, CTB_ERR_ARG, "n out of range [0, 2^31)");
   if (n > 0 && !xyz) return fail(c, CTB_ERR_ARG, "xyz is NULL");
@@ -326,6 +341,7 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   if (r) return r;
   c->n = -1;
   c->batch_keys = nullptr;
+  c->pairsum_segs = 0;
   const double* dxyz = xyz;
   const double* dw = w;
   if (n > 0 && !is_device_ptr(xyz)) {
@@ -343,7 +359,7 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   CK(c, cudaMemsetAsync(c->flags.p, 0, 64, c->st));
 
   // units and grid
-  int cpr = c->cells_per_rmax > 0 ? c->cells_per_rmax : 8;
+  const int cpr = grid_cells_per_rmax(c);
   Geom g{};
   g.periodic = c->periodic;
   g.nbins = c->nbins;
@@ -456,8 +472,15 @@ struct PairPlan {
   int64_t chunk_first;   // primaries in the first chunk (from the mean density)
   int64_t chunk_max;     // primaries per chunk at most
   uint64_t list_cap;     // neighbour-list entries per chunk at most
-  int nparts;
+  uint64_t code_cap;     // candidate bin codes (bytes) per chunk at most
+  double cand_first;     // candidates per primary assumed for the first chunk
+  int nparts;            // pair-sum partial rows (blocks of k_pair_sums)
+  int ncon;              // contraction partial rows (blocks of the contraction kernel in use)
 };
+
+// Bin-code buffer bound: one byte per candidate of a chunk, at most four per
+// list entry of the list capacity.
+constexpr uint64_t kCodeCap = 1ull << 34;
 
 int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   int wpb = c->wpb > 0 ? c->wpb : 4;
@@ -474,12 +497,24 @@ int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   pl->chunk_max = std::max<int64_t>(1, std::min<int64_t>(chunk, std::max<int64_t>(np, 1)));
   pl->list_cap = c->list_cap;
   pl->nparts = 2 * c->nsm;
+  if (c->precision == CTB_PREC_FP32) {
+    // one wave of the FP32 contraction's resident blocks
+    const int cb = contract_fp32_blocks_per_sm(c->nbins, c->lmax, c->lay.row);
+    if (cb < 1) return fail(c, CTB_ERR_CUDA, "the contraction kernel cannot be resident");
+    pl->ncon = cb * c->nsm;
+  } else {
+    pl->ncon = 2 * c->nsm;
+  }
   // first chunk from the mean density, with a margin for clustering; later
   // chunks follow the measured pairs per primary
   const double vol = c->periodic ? c->box * c->box * c->box : c->bbox_volume;
   const double ball = 4.0 / 3.0 * M_PI * (c->rmax * c->rmax * c->rmax - c->rmin * c->rmin * c->rmin);
   const double est = vol > 0 ? 2.0 * (double)c->n * std::min(1.0, ball / vol) + 64.0 : 64.0;
-  pl->chunk_first = std::max<int64_t>(1, std::min<int64_t>(pl->chunk_max, (int64_t)(0.9 * (double)pl->list_cap / est)));
+  // candidates (points of the scanned cell rows) run about 1.3-1.5x the pairs
+  pl->code_cap = std::min<uint64_t>(kCodeCap, 4 * pl->list_cap);
+  pl->cand_first = 1.5 * est;
+  const double first = std::min(0.9 * (double)pl->list_cap / est, 0.9 * (double)pl->code_cap / pl->cand_first);
+  pl->chunk_first = std::max<int64_t>(1, std::min<int64_t>(pl->chunk_max, (int64_t)first));
   return CTB_OK;
 }
 
@@ -506,6 +541,9 @@ int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, siz
   const size_t rowsz = (size_t)nb * c->lay.row;
   const float* M = P<float>(c->M) + (size_t)off * rowsz;
   const float* wp = P<float>(c->wprim) + off;
+  // two-point pair sums from the a_00 column (every precision)
+  CK(c, launch_pair_sums(M, wp, cnt, nb, c->lay.row, c->lay.slot[0],
+                         P<double>(c->pairsum) + seg * pl.nparts * nb, pl.nparts, c->st));
   if (c->precision != CTB_PREC_FP32) {
     const bool tf32 = c->precision == CTB_PREC_TF32;
     std::vector<unsigned long long> lb, kp;
@@ -525,8 +563,8 @@ int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, siz
                       P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p, c->ops[2].p, c->ops[3].p, c->st));
     CK(c, cudaEventRecord(*ev_pack, c->st));
     CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), c->ops[0].p, c->ops[1].p, c->ops[2].p,
-                             c->ops[3].p, P<double>(c->partial_tc) + seg * pl.nparts * zsz, pl.nparts,
-                             P<unsigned int>(c->flags) + 1, c->st));
+                             c->ops[3].p, P<double>(c->partial_tc) + seg * pl.ncon * zsz, pl.ncon,
+                             P<unsigned int>(c->flags) + 1, c->inject == CTB_INJECT_STALL, c->st));
     // the host vectors lb / kp back the copies above: wait before releasing them
     CK(c, cudaStreamSynchronize(c->st));
   } else {
@@ -538,9 +576,9 @@ int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, siz
     ca.lmax = c->lmax;
     ca.row = c->lay.row;
     ca.slot = P<int>(c->slot);
-    ca.partial = P<double>(c->partial) + seg * pl.nparts * zsz;
+    ca.partial = P<double>(c->partial) + seg * pl.ncon * zsz;
     ca.part0 = 0;
-    CK(c, launch_contract_fp32(ca, pl.nparts, c->st));
+    CK(c, launch_contract_fp32(ca, pl.ncon, c->st));
   }
   return CTB_OK;
 }
@@ -554,8 +592,10 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   CK(c, ensure(c, c->M, (size_t)pl.chunk_max * nb * c->lay.row * sizeof(float)));
   CK(c, ensure(c, c->wprim, (size_t)pl.chunk_max * sizeof(float)));
   CK(c, ensure(c, c->counters, 64));
+  CK(c, ensure(c, c->code_base, (size_t)pl.chunk_max * row_blocks(c->g) * sizeof(unsigned long long)));
   unsigned long long* work = P<unsigned long long>(c->counters);
   unsigned long long* total = work + 1;
+  unsigned long long* code_total = work + 2;
   StreamArgs sa{};
   sa.pts = P<uint4>(c->pts);
   sa.cell_start = P<uint32_t>(c->cell_start);
@@ -567,6 +607,8 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   sa.work = work;
   sa.total = total;
   sa.keys = c->batch_keys;
+  sa.code_total = code_total;
+  sa.code_base = P<unsigned long long>(c->code_base);
   sa.g = c->g;
   AlmArgs aa{};
   aa.pts = P<uint4>(c->pts);
@@ -584,6 +626,8 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   double t_stream = 0, t_alm = 0, t_con = 0, t_pack = 0;
   uint64_t pairs = 0, chunks = 0;
   int64_t C = pl.chunk_first;
+  double cand_per = pl.cand_first;  // candidates per primary (estimate, then measured)
+  size_t codes_need = 0;            // bytes the last count of this chunk asked for
   int64_t c0 = 0;
   // [0] count start [1] count end [2] fill end [3] alm end [4] contraction end [5] pack end
   cudaEvent_t* ev = c->ev + 2;
@@ -591,23 +635,37 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     const int64_t cnt = std::min(C, np - c0);
     sa.prim_begin = aa.prim_begin = c0;
     sa.prim_count = aa.prim_count = cnt;
-    CK(c, cudaMemsetAsync(work, 0, 16, c->st));
+    // bin codes of this chunk: the estimate, or what its last count asked for
+    const size_t codes_want = std::max<size_t>(
+        codes_need, (size_t)std::min<double>((double)pl.code_cap, 1.05 * cand_per * (double)cnt + 256.0));
+    CK(c, ensure(c, c->codes, codes_want));
+    sa.codes = P<uint8_t>(c->codes);
+    sa.code_cap = c->codes.bytes;
+    CK(c, cudaMemsetAsync(work, 0, 24, c->st));
     CK(c, cudaEventRecord(ev[0], c->st));
     sa.lists = nullptr;
     CK(c, launch_stream(sa, false, pl.count_blocks, c->st));
     CK(c, cudaEventRecord(ev[1], c->st));
-    unsigned long long tot = 0;
-    CK(c, cudaMemcpyAsync(&tot, total, sizeof(tot), cudaMemcpyDeviceToHost, c->st));
+    unsigned long long tc[2] = {0, 0};  // pairs, candidates
+    CK(c, cudaMemcpyAsync(tc, total, sizeof(tc), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
     t_stream += elapsed(ev[0], ev[1]);
-    if (tot > pl.list_cap) {
+    const unsigned long long tot = tc[0], ctot = tc[1];
+    if (tot > pl.list_cap || ctot > pl.code_cap) {
       if (cnt > 1) {
         C = std::max<int64_t>(1, cnt / 2);
+        codes_need = 0;
         continue;
       }
-      return fail(c, CTB_ERR_OOM, "one primary has more neighbours than the list buffer holds");
+      return fail(c, CTB_ERR_OOM, "one primary has more neighbours than the list buffers hold");
     }
-    CK(c, ensure(c, c->lists, std::max<size_t>((size_t)tot, 1) * 4));
+    if (ctot > c->codes.bytes) {
+      // the codes did not fit: grow the buffer and count this chunk again
+      codes_need = (size_t)ctot;
+      continue;
+    }
+    codes_need = 0;
+    CK(c, ensure(c, c->lists, std::max<size_t>((size_t)tot, 1) * 4 + kListSlackBytes));
     CK(c, exclusive_scan_u32(P<uint32_t>(c->counts), P<uint32_t>(c->offsets), (size_t)cnt * nb,
                              P<uint32_t>(c->scan_tmp2), c->st));
     sa.lists = P<uint32_t>(c->lists);
@@ -655,10 +713,12 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     pairs += tot;
     ++chunks;
     c0 += cnt;
-    // next chunk: fill about 90 % of the list buffer at the observed density
+    // next chunk: fill about 90 % of the list and code buffers at the observed density
     const double per = cnt > 0 ? (double)tot / (double)cnt : 0.0;
-    int64_t nxt = per > 0 ? (int64_t)(0.9 * (double)pl.list_cap / per) : pl.chunk_max;
-    C = std::max<int64_t>(1, std::min<int64_t>(nxt, pl.chunk_max));
+    if (cnt > 0) cand_per = std::max(1.0, (double)ctot / (double)cnt);
+    double nxt = per > 0 ? 0.9 * (double)pl.list_cap / per : (double)pl.chunk_max;
+    nxt = std::min(nxt, 0.9 * (double)pl.code_cap / cand_per);
+    C = std::max<int64_t>(1, std::min<int64_t>((int64_t)nxt, pl.chunk_max));
   }
   c->t_ms[2] = t_stream + t_alm;
   c->t_ms[3] = t_pack;
@@ -680,13 +740,16 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
   r = plan_pairs(c, np, &pl);
   if (r) return r;
   const size_t zsz = (size_t)(c->lmax + 1) * c->nbins * c->nbins;
-  CK(c, ensure(c, c->partial, (size_t)pl.nparts * zsz * sizeof(double)));
+  CK(c, ensure(c, c->partial, (size_t)pl.ncon * zsz * sizeof(double)));
   CK(c, ensure(c, c->zeta, zsz * sizeof(double)));
-  CK(c, cudaMemsetAsync(c->partial.p, 0, (size_t)pl.nparts * zsz * sizeof(double), c->st));
+  CK(c, cudaMemsetAsync(c->partial.p, 0, (size_t)pl.ncon * zsz * sizeof(double), c->st));
+  c->pairsum_segs = 0;
+  CK(c, ensure(c, c->pairsum, (size_t)pl.nparts * c->nbins * sizeof(double)));
+  CK(c, cudaMemsetAsync(c->pairsum.p, 0, (size_t)pl.nparts * c->nbins * sizeof(double), c->st));
   const bool tc = c->precision != CTB_PREC_FP32;
   if (tc) {
-    CK(c, ensure(c, c->partial_tc, (size_t)pl.nparts * zsz * sizeof(double)));
-    CK(c, cudaMemsetAsync(c->partial_tc.p, 0, (size_t)pl.nparts * zsz * sizeof(double), c->st));
+    CK(c, ensure(c, c->partial_tc, (size_t)pl.ncon * zsz * sizeof(double)));
+    CK(c, cudaMemsetAsync(c->partial_tc.p, 0, (size_t)pl.ncon * zsz * sizeof(double), c->st));
     CK(c, cudaMemsetAsync(P<unsigned int>(c->flags) + 1, 0, 4, c->st));
   }
   for (int k = 2; k < kStages; ++k) c->t_ms[k] = 0;  // [0], [1]: the last ctb_set_points
@@ -696,9 +759,9 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
   const int evs = 2 + 8;
   CK(c, cudaEventRecord(c->ev[evs], c->st));
   if (tc)
-    CK(c, launch_finalize_tc(P<double>(c->partial_tc), c->lmax, pl.nparts, c->nbins, P<double>(c->zeta), c->st));
+    CK(c, launch_finalize_tc(P<double>(c->partial_tc), c->lmax, pl.ncon, c->nbins, P<double>(c->zeta), c->st));
   else
-    CK(c, launch_finalize(P<double>(c->partial), pl.nparts, c->lmax, c->nbins, P<double>(c->zeta), c->st));
+    CK(c, launch_finalize(P<double>(c->partial), pl.ncon, c->lmax, c->nbins, P<double>(c->zeta), c->st));
   CK(c, cudaEventRecord(c->ev[evs + 1], c->st));
   const bool dev_out = is_device_ptr(zeta_out);
   CK(c, cudaMemcpyAsync(zeta_out, c->zeta.p, zsz * sizeof(double),
@@ -709,6 +772,8 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
   c->npairs = pairs;
   c->t_ms[5] = elapsed(c->ev[evs], c->ev[evs + 1]);
   if (tc_err) return fail(c, CTB_ERR_TIMEOUT, "tensor-core contraction: a bounded wait timed out");
+  c->pairsum_segs = 1;
+  c->pairsum_parts = pl.nparts;
   return CTB_OK;
 }
 
@@ -739,7 +804,7 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   c->n = -1;
   c->batch_keys = nullptr;
   // grid of one periodic catalogue
-  const int cpr = c->cells_per_rmax > 0 ? c->cells_per_rmax : 8;
+  const int cpr = grid_cells_per_rmax(c);
   Geom g{};
   g.periodic = 1;
   g.nbins = c->nbins;
@@ -819,12 +884,15 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   }
   const size_t zsz = (size_t)(c->lmax + 1) * c->nbins * c->nbins;
   const size_t budget = (size_t)2 << 30;
-  pl.nparts = (int)std::max<size_t>(8, std::min<size_t>((size_t)pl.nparts, budget / ((size_t)k * zsz * 8)));
+  pl.ncon = (int)std::max<size_t>(8, std::min<size_t>((size_t)pl.ncon, budget / ((size_t)k * zsz * 8)));
   const bool tc = c->precision != CTB_PREC_FP32;
   Buf& part = tc ? c->partial_tc : c->partial;
-  CK(c, ensure(c, part, (size_t)k * pl.nparts * zsz * sizeof(double)));
-  CK(c, cudaMemsetAsync(part.p, 0, (size_t)k * pl.nparts * zsz * sizeof(double), c->st));
+  CK(c, ensure(c, part, (size_t)k * pl.ncon * zsz * sizeof(double)));
+  CK(c, cudaMemsetAsync(part.p, 0, (size_t)k * pl.ncon * zsz * sizeof(double), c->st));
   if (tc) CK(c, cudaMemsetAsync(P<unsigned int>(c->flags) + 1, 0, 4, c->st));
+  c->pairsum_segs = 0;
+  CK(c, ensure(c, c->pairsum, (size_t)k * pl.nparts * c->nbins * sizeof(double)));
+  CK(c, cudaMemsetAsync(c->pairsum.p, 0, (size_t)k * pl.nparts * c->nbins * sizeof(double), c->st));
   CK(c, ensure(c, c->zeta, (size_t)k * zsz * sizeof(double)));
   for (int i = 0; i < kStages; ++i) c->t_ms[i] = 0;
   std::vector<int64_t> seg_end(cum.begin() + 1, cum.end());
@@ -834,12 +902,12 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   if (r) return r;
   CK(c, cudaEventRecord(c->ev[10], c->st));
   for (int i = 0; i < k; ++i) {
-    const double* pi = P<double>(part) + (size_t)i * pl.nparts * zsz;
+    const double* pi = P<double>(part) + (size_t)i * pl.ncon * zsz;
     double* zi = P<double>(c->zeta) + (size_t)i * zsz;
     if (tc)
-      CK(c, launch_finalize_tc(pi, c->lmax, pl.nparts, c->nbins, zi, c->st));
+      CK(c, launch_finalize_tc(pi, c->lmax, pl.ncon, c->nbins, zi, c->st));
     else
-      CK(c, launch_finalize(pi, pl.nparts, c->lmax, c->nbins, zi, c->st));
+      CK(c, launch_finalize(pi, pl.ncon, c->lmax, c->nbins, zi, c->st));
   }
   CK(c, cudaEventRecord(c->ev[11], c->st));
   const bool dev_out = is_device_ptr(zeta_out);
@@ -853,6 +921,8 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   c->t_ms[1] = t_sort;
   c->t_ms[5] = elapsed(c->ev[10], c->ev[11]);
   if (tc_err) return fail(c, CTB_ERR_TIMEOUT, "tensor-core contraction: a bounded wait timed out");
+  c->pairsum_segs = k;
+  c->pairsum_parts = pl.nparts;
   return CTB_OK;
 }
 
@@ -900,6 +970,60 @@ int map_primaries(ctb_ctx* c, const int64_t* idx, int64_t m) {
 
 // ===========================================================================
 // C ABI
+
+// ---------------------------------------------------------------------------
+// Autotuner: the grid's cells per r_max (the cell size h = r_max / k).  Each
+// candidate grids the catalogue, then the pair kernels (enumeration and
+// accumulation, no contraction) run twice on the same sample of primaries:
+// eight runs of consecutive primaries in cell order, spread over the
+// catalogue, so their neighbourhoods are as local as in a full pass.  The
+// second run is timed; the fastest candidate is kept for this context.
+
+int autotune_grid(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
+  static const int kCand[] = {3, 4, 6, 8, 12, 16};
+  int best = 8;
+  float best_ms = INFINITY;
+  uint32_t prev_nc = 0;
+  for (int cpr : kCand) {
+    c->tuned_cpr = cpr;
+    int r = load_points(c, xyz, w, n);
+    if (r) return r;
+    if (c->g.nc == prev_nc) continue;  // clamped to the same grid
+    prev_nc = c->g.nc;
+    r = ensure_tables(c);
+    if (r) return r;
+    // sample size: about 5e8 pairs at the mean density, 256..8192 primaries
+    const double vol = c->periodic ? c->box * c->box * c->box : c->bbox_volume;
+    const double ball = 4.0 / 3.0 * M_PI * (c->rmax * c->rmax * c->rmax - c->rmin * c->rmin * c->rmin);
+    const double per = vol > 0 ? (double)n * std::min(1.0, ball / vol) + 1.0 : 1.0;
+    const int64_t S = std::min<int64_t>(n, std::max<int64_t>(256, std::min<int64_t>(8192, (int64_t)(5e8 / per))));
+    std::vector<uint32_t> sample;
+    sample.reserve((size_t)S);
+    const int64_t runs = 8, len = std::max<int64_t>(1, S / runs);
+    for (int64_t k = 0; k < runs && (int64_t)sample.size() < S; ++k) {
+      const int64_t s0 = std::min<int64_t>(n - len, k * n / runs);
+      for (int64_t q = 0; q < len && (int64_t)sample.size() < S; ++q) sample.push_back((uint32_t)(s0 + q));
+    }
+    const int64_t m = (int64_t)sample.size();
+    CK(c, ensure(c, c->prim, (size_t)m * 4));
+    CK(c, cudaMemcpyAsync(c->prim.p, sample.data(), (size_t)m * 4, cudaMemcpyHostToDevice, c->st));
+    PairPlan pl{};
+    r = plan_pairs(c, m, &pl);
+    if (r) return r;
+    uint64_t pairs = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      r = run_pairs(c, P<uint32_t>(c->prim), m, false, pl, nullptr, &pairs);
+      if (r) return r;
+    }
+    const float ms = (float)(c->t_ms[6] + c->t_ms[7]);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cpr;
+    }
+  }
+  c->tuned_cpr = best;
+  return CTB_OK;
+}
 
 extern "C" {
 
@@ -961,6 +1085,13 @@ const char* ctb_last_error(const ctb_ctx* c) { return c ? c->err.c_str() : g_cre
 
 int ctb_set_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   if (!c) return CTB_ERR_ARG;
+  if (c->autotune && c->cells_per_rmax == 0 && c->tuned_cpr == 0 && n > 1) {
+    int r = autotune_grid(c, xyz, w, n);
+    if (r) {
+      c->tuned_cpr = 0;
+      return r;
+    }
+  }
   const unsigned long long l0 = g_launches;
   int r = load_points(c, xyz, w, n);
   c->launches_points = g_launches - l0;
@@ -1036,9 +1167,10 @@ int ctb_set_option(ctb_ctx* c, int key, int64_t v) {
       c->cells_per_rmax = (int)v;
       c->n = -1;  // grid changes: the catalogue must be reloaded
       return CTB_OK;
-    case CTB_OPT_BIN_CAPACITY:
-      if (v < 256 || v > 65536) return fail(c, CTB_ERR_ARG, "bin capacity out of range [256, 65536]");
-      c->cap = (uint32_t)((v + 3) & ~3);
+    case CTB_OPT_LIST_CAPACITY:
+      if (v != 0 && (v < 4096 || v > ((int64_t)1 << 32)))
+        return fail(c, CTB_ERR_ARG, "list capacity must be 0 or in [4096, 2^32]");
+      c->list_cap = v == 0 ? (uint64_t)1 << 32 : (uint64_t)v;
       return CTB_OK;
     case CTB_OPT_WARPS_PER_BLOCK:
       if (v < 0 || v > 16) return fail(c, CTB_ERR_ARG, "warps per block out of range [0, 16]");
@@ -1047,6 +1179,15 @@ int ctb_set_option(ctb_ctx* c, int key, int64_t v) {
     case CTB_OPT_CHUNK_PRIMARIES:
       if (v != 0 && v < 1024) return fail(c, CTB_ERR_ARG, "chunk must be 0 or >= 1024");
       c->chunk = v;
+      return CTB_OK;
+    case CTB_OPT_FAULT_INJECT:
+      if (v != 0 && v != CTB_INJECT_STALL && v != CTB_INJECT_ALLOC) return fail(c, CTB_ERR_ARG, "unknown fault");
+      c->inject = (int)v;
+      return CTB_OK;
+    case CTB_OPT_AUTOTUNE:
+      if (v != 0 && v != 1) return fail(c, CTB_ERR_ARG, "autotune must be 0 or 1");
+      c->autotune = (int)v;
+      c->tuned_cpr = 0;  // (re)tune on the next ctb_set_points
       return CTB_OK;
     case CTB_OPT_DETERMINISTIC:
       if (v != 0 && v != 1) return fail(c, CTB_ERR_ARG, "deterministic must be 0 or 1");
@@ -1092,6 +1233,56 @@ int ctb_get_launch_count(ctb_ctx* c, uint64_t* kernels) {
 int ctb_get_pair_count(ctb_ctx* c, uint64_t* pairs) {
   if (!c || !pairs) return CTB_ERR_ARG;
   *pairs = c->npairs;
+  return CTB_OK;
+}
+
+int ctb_edge_correct(ctb_ctx* c, const double* zeta_nnn, const double* zeta_rrr, double* zeta_out) {
+  if (!c) return CTB_ERR_ARG;
+  if (!zeta_nnn || !zeta_rrr || !zeta_out) return fail(c, CTB_ERR_ARG, "NULL argument");
+  CK(c, cudaSetDevice(c->dev));
+  const int n = c->lmax + 1, nb = c->nbins;
+  const size_t zsz = (size_t)n * nb * nb;
+  // the 3j table, then both inputs and the output in device memory (staged when on the host)
+  std::vector<double> tj;
+  make_threej_table(c->lmax, tj);
+  CK(c, ensure(c, c->edge_tj, tj.size() * sizeof(double)));
+  CK(c, ensure(c, c->edge_in, 3 * zsz * sizeof(double)));
+  double* dn = P<double>(c->edge_in);
+  double* dr = dn + zsz;
+  double* dout = dr + zsz;
+  CK(c, cudaMemcpyAsync(c->edge_tj.p, tj.data(), tj.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(dn, zeta_nnn, zsz * sizeof(double), cudaMemcpyDefault, c->st));
+  CK(c, cudaMemcpyAsync(dr, zeta_rrr, zsz * sizeof(double), cudaMemcpyDefault, c->st));
+  CK(c, launch_edge_correct(dn, dr, P<double>(c->edge_tj), c->lmax, nb, dout, c->st));
+  CK(c, cudaMemcpyAsync(zeta_out, dout, zsz * sizeof(double), cudaMemcpyDefault, c->st));
+  CK(c, cudaStreamSynchronize(c->st));  // the host table and host outputs are done with
+  return CTB_OK;
+}
+
+int ctb_get_2pcf(ctb_ctx* c, double* out, int cap) {
+  if (!c || !out) return CTB_ERR_ARG;
+  if (c->pairsum_segs <= 0) return fail(c, CTB_ERR_STATE, "no zeta computed on this catalogue yet");
+  const int nb = c->nbins, nseg = c->pairsum_segs, np = c->pairsum_parts;
+  if ((int64_t)cap < (int64_t)nseg * nb) return fail(c, CTB_ERR_ARG, "out holds fewer than catalogues * nbins values");
+  CK(c, cudaSetDevice(c->dev));
+  std::vector<double> part((size_t)nseg * np * nb);
+  CK(c, cudaMemcpyAsync(part.data(), c->pairsum.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  const double s4pi = std::sqrt(4.0 * M_PI);  // a_00 = sum_j w_j / sqrt(4 pi)
+  for (int k = 0; k < nseg; ++k)
+    for (int b = 0; b < nb; ++b) {
+      double s = 0.0;
+      for (int p = 0; p < np; ++p) s += part[((size_t)k * np + p) * nb + b];
+      out[(size_t)k * nb + b] = s4pi * s;
+    }
+  return nseg * nb;
+}
+
+int ctb_get_grid(ctb_ctx* c, int* cells_per_rmax, int* cells_per_axis) {
+  if (!c || !cells_per_rmax || !cells_per_axis) return CTB_ERR_ARG;
+  if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
+  *cells_per_rmax = grid_cells_per_rmax(c);
+  *cells_per_axis = (int)c->g.nc;
   return CTB_OK;
 }
 

@@ -9,120 +9,191 @@
 
 namespace ctb {
 
-constexpr int kConThreads = 512;
-constexpr int kConMaxPer = 24;       // entries per thread (registers)
-constexpr int kConFlush = 64;        // primaries per FP32 partial before FP64
-constexpr int kConSmemFloats = 24576;  // 96 KB of staged rows
-constexpr int kConGroup = kConThreads * kConMaxPer;  // entries per block (grid.y splits more)
+// Register-tiled form.  For one l, zeta~_l restricted to bins [4B1, 4B1+4) x
+// [4B2, 4B2+4) is a 4x4 tile: per primary and per m, one 16-byte shared load
+// of each side (bins contiguous) and 16 FMAs.  Work split of a block:
+//   warp  -> a multipole pair (l, L - l) (one l when l = L - l), so every warp
+//            does 2L + 2 m-steps per primary and no lane diverges on l;
+//            pairs with more than 32 tiles take several warps
+//   lane  -> a tile B1 <= B2 and an m-group g: lanes of the same tile split the
+//            m-steps (m = g, g + G, ...) and are added in group order at the end
+// The block stages a few primaries' rows transposed to [primary][l^2+l+m][bin]
+// (bins padded to a multiple of 4 with zeros).  FP32 over the block's slice of
+// the launch's primaries, then one FP64 add per (l, b1 <= b2) entry, whose
+// owner is a single lane: the partial sums are deterministic.
+constexpr int kConTile = 4;
+constexpr int kConMaxThreads = 512;
+constexpr int kConStageFloats = 10240;  // 40 KB of staged rows: several blocks per SM
 
-// Block (x, y) owns partial row (part0 + x), a contiguous range of primaries,
-// and entries [y * kConGroup, (y+1) * kConGroup) of the upper triangle
-// (l, b1 <= b2); each thread owns up to kConMaxPer of them.  Staged rows use
-// an odd smem stride (row + 1 floats) so that lanes reading the same slot of
-// different bins hit different banks.  FP32 sums over kConFlush primaries,
-// then FP64.
-__global__ void __launch_bounds__(kConThreads) k_contract_fp32(ContractArgs a) {
-  extern __shared__ float s_dyn[];
-  __shared__ int s_slot[(kLmaxCap + 1) * (kLmaxCap + 1)];
-  const int nb = a.nbins, row = a.row, srow = a.row + 1;
-  const int rowsz = nb * row, srowsz = nb * srow;
-  const int rows_cap = srowsz > kConSmemFloats ? srowsz : kConSmemFloats;
-  float* s_rows = s_dyn;
-  const int T = nb * (nb + 1) / 2;
-  const int e_lo = blockIdx.y * kConGroup;
-  const int E = min((a.lmax + 1) * T - e_lo, kConGroup);
-  const int nc = (a.lmax + 1) * (a.lmax + 1);
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) s_slot[c] = a.slot[c];
-  uint32_t md[kConMaxPer];
+struct ConShape {
+  int nbb, tiles, G, warps_per_pair, pairs, pairs_per_block, ny, threads, Q, per, red_floats, tab_ints,
+      smem_floats;
+};
+
+__host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row) {
+  ConShape c{};
+  c.nbb = (nbins + kConTile - 1) / kConTile;
+  c.tiles = c.nbb * (c.nbb + 1) / 2;
+  c.warps_per_pair = (c.tiles + 31) / 32;
+  c.G = c.tiles >= 32 ? 1 : 32 / c.tiles;
+  c.pairs = lmax / 2 + 1;
+  // at most kConMaxThreads a block: more pairs go to further blocks in y
+  c.pairs_per_block = kConMaxThreads / (32 * c.warps_per_pair);
+  if (c.pairs_per_block > c.pairs) c.pairs_per_block = c.pairs;
+  c.ny = (c.pairs + c.pairs_per_block - 1) / c.pairs_per_block;
+  c.threads = 32 * c.warps_per_pair * c.pairs_per_block;
+  const int nc = (lmax + 1) * (lmax + 1);
+  c.per = nc * c.nbb * kConTile;
+  c.Q = c.per >= kConStageFloats ? 1 : kConStageFloats / c.per;
+  c.red_floats = c.G > 1 ? (c.threads / 32) * 32 * 17 : 0;
+  c.tab_ints = (row + 3) & ~3;  // row slot -> l^2 + l + m, or -1
+  c.smem_floats = c.tab_ints + c.Q * c.per + c.red_floats;
+  return c;
+}
+
+// 4x4 tile of one l: acc[i][j] += w * sum_{m in group} x_i y_j
+__device__ __forceinline__ void con_tile(const float* __restrict__ S, int nbp, int l, int g, int G, int B1, int B2,
+                                         float w, float (&acc)[16]) {
+  const int s0 = l * l;
+  for (int m = g; m <= 2 * l; m += G) {
+    const float4 x = *reinterpret_cast<const float4*>(S + (s0 + m) * nbp + 4 * B1);
+    const float4 y = *reinterpret_cast<const float4*>(S + (s0 + m) * nbp + 4 * B2);
+    const float xs[4] = {w * x.x, w * x.y, w * x.z, w * x.w};
+    const float ys[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-  for (int k = 0; k < kConMaxPer; ++k) {
-    const int e = threadIdx.x + k * kConThreads;
-    md[k] = 0;
-    if (e < E) {
-      int l = (e + e_lo) / T, r = (e + e_lo) % T, b1 = 0;
-      while (r >= nb - b1) {
-        r -= nb - b1;
-        ++b1;
-      }
-      const int b2 = b1 + r;
-      md[k] = (uint32_t)l | ((uint32_t)b1 << 5) | ((uint32_t)b2 << 11);
-    }
-  }
-  const int64_t per = (a.np + gridDim.x - 1) / gridDim.x;
-  const int64_t p0 = (int64_t)blockIdx.x * per;
-  const int64_t p1 = min(a.np, p0 + per);
-  const int stage = rows_cap / srowsz;
-  float acc[kConMaxPer];
-  double acc64[kConMaxPer];
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-  for (int k = 0; k < kConMaxPer; ++k) {
-    acc[k] = 0.f;
-    acc64[k] = 0.0;
-  }
-  int since = 0;
-  __syncthreads();
-  for (int64_t pb = p0; pb < p1; pb += stage) {
-    const int cnt = (int)min((int64_t)stage, p1 - pb);
-    const float* src = a.M + (uint64_t)pb * rowsz;
-    for (int k = threadIdx.x; k < cnt * rowsz; k += blockDim.x) {
-      const int rr = k / row, cc = k - rr * row;  // rr = primary * nb + bin
-      s_rows[rr * srow + cc] = __ldcs(src + k);
-    }
-    __syncthreads();
-    for (int q = 0; q < cnt; ++q) {
-      const float wp = a.wprim[pb + q];
-      const float* A = s_rows + q * srowsz;
-#pragma unroll
-      for (int k = 0; k < kConMaxPer; ++k) {
-        const int e = threadIdx.x + k * kConThreads;
-        if (e < E) {
-          const uint32_t m = md[k];
-          const int l = m & 31, b1 = (m >> 5) & 63, b2 = (m >> 11) & 63;
-          const float* A1 = A + b1 * srow;
-          const float* A2 = A + b2 * srow;
-          const int c0 = l * l;
-          float s = 0.f;
-          for (int c = c0; c <= c0 + 2 * l; ++c) {
-            const int sl = s_slot[c];
-            s = fmaf(A1[sl], A2[sl], s);
-          }
-          acc[k] = fmaf(wp, s, acc[k]);
-        }
-      }
-      if (++since == kConFlush) {
-        since = 0;
-#pragma unroll
-        for (int k = 0; k < kConMaxPer; ++k) {
-          acc64[k] += (double)acc[k];
-          acc[k] = 0.f;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  double* out = a.partial + (size_t)(a.part0 + blockIdx.x) * (a.lmax + 1) * nb * nb;
-#pragma unroll
-  for (int k = 0; k < kConMaxPer; ++k) {
-    const int e = threadIdx.x + k * kConThreads;
-    if (e < E) {
-      const uint32_t m = md[k];
-      const int l = m & 31, b1 = (m >> 5) & 63, b2 = (m >> 11) & 63;
-      out[((size_t)l * nb + b1) * nb + b2] += acc64[k] + (double)acc[k];
-    }
+      for (int j = 0; j < 4; ++j) acc[i * 4 + j] = fmaf(xs[i], ys[j], acc[i * 4 + j]);
   }
 }
 
+__device__ __forceinline__ void con_flush(const ConShape& sh, const float (&acc)[16], int l, int tile, int g, int B1,
+                                          int B2, int nb, int lmax, double* __restrict__ out, float* s_red,
+                                          int lane) {
+  // lanes of one tile: add the m-groups in order through shared memory
+  float* mine = s_red + lane * 17;
+  if (sh.G > 1) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) mine[k] = acc[k];
+  }
+  __syncwarp();
+  if (g == 0 && tile < sh.tiles && l <= lmax) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      float v = acc[k];
+      for (int h = 1; h < sh.G; ++h) v += s_red[(lane + h * sh.tiles) * 17 + k];
+      const int b1 = 4 * B1 + k / 4, b2 = 4 * B2 + k % 4;
+      if (b1 < nb && b2 < nb && b1 <= b2) out[((size_t)l * nb + b1) * nb + b2] += (double)v;
+    }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kConMaxThreads, 1) k_contract_fp32(ContractArgs a) {
+  extern __shared__ float s_dyn[];
+  const int nb = a.nbins, L = a.lmax, nc = (L + 1) * (L + 1);
+  const ConShape sh = con_shape(nb, L, a.row);
+  const int nbp = sh.nbb * kConTile;
+  const int per = sh.per;
+  // [row slot -> coefficient table | Q staged primaries | per-warp m-group combine buffers]
+  int* s_inv = reinterpret_cast<int*>(s_dyn);
+  float* s_rows = s_dyn + sh.tab_ints;
+  float* s_red_all = s_rows + sh.Q * per;
+  for (int k = threadIdx.x; k < a.row; k += blockDim.x) s_inv[k] = -1;
+  for (int k = threadIdx.x; k < sh.Q * per; k += blockDim.x) s_rows[k] = 0.f;  // bin padding stays zero
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) s_inv[a.slot[c]] = c;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pair = blockIdx.y * sh.pairs_per_block + warp / sh.warps_per_pair;
+  const int part = warp % sh.warps_per_pair;
+  const int la = pair, lb = L - pair;
+  const int tl = lane % (sh.G == 1 ? 32 : sh.tiles);
+  const int g = sh.G == 1 ? 0 : lane / sh.tiles;
+  const int tile = part * 32 + tl;
+  const bool active = pair < sh.pairs && tile < sh.tiles && g < sh.G;
+  int B1 = 0, B2 = 0;
+  {
+    int r = active ? tile : 0;
+    while (r >= sh.nbb - B1) {
+      r -= sh.nbb - B1;
+      ++B1;
+    }
+    B2 = B1 + r;
+  }
+  float acc_a[16], acc_b[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc_a[k] = acc_b[k] = 0.f;
+  const int64_t slice = (a.np + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = (int64_t)blockIdx.x * slice;
+  const int64_t p1 = min(a.np, p0 + slice);
+  const int rowsz = nb * a.row;
+  const bool vec4 = (a.row & 3) == 0 && (reinterpret_cast<uintptr_t>(a.M) & 15) == 0;
+  for (int64_t pb = p0; pb < p1; pb += sh.Q) {
+    const int cnt = (int)min((int64_t)sh.Q, p1 - pb);
+    __syncthreads();  // the previous primaries are done (and the tables / zero fill on entry)
+    // coalesced loads of the rows (16 bytes when rows and base allow it),
+    // scattered to [primary][coefficient][bin]
+    if (vec4) {
+      const float4* src = reinterpret_cast<const float4*>(a.M + (uint64_t)pb * rowsz);
+      const int row4 = a.row >> 2;
+      for (int k = threadIdx.x; k < cnt * nb * row4; k += blockDim.x) {
+        const int pr = k / row4, c4 = k - pr * row4;  // pr = primary * nb + bin
+        const int q = pr / nb, b = pr - q * nb;
+        const float4 v = __ldcs(src + k);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+        float* dst = s_rows + q * per + b;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = s_inv[4 * c4 + i];
+          if (c >= 0) dst[c * nbp] = e[i];
+        }
+      }
+    } else {
+      const float* src = a.M + (uint64_t)pb * rowsz;
+      for (int k = threadIdx.x; k < cnt * nb * a.row; k += blockDim.x) {
+        const int pr = k / a.row, sl = k - pr * a.row;
+        const int q = pr / nb, b = pr - q * nb;
+        const int c = s_inv[sl];
+        if (c >= 0) s_rows[q * per + c * nbp + b] = __ldcs(src + k);
+      }
+    }
+    __syncthreads();
+    if (active) {
+      for (int q = 0; q < cnt; ++q) {
+        const float w = a.wprim[pb + q];
+        const float* S = s_rows + q * per;
+        con_tile(S, nbp, la, g, sh.G, B1, B2, w, acc_a);
+        if (lb != la) con_tile(S, nbp, lb, g, sh.G, B1, B2, w, acc_b);
+      }
+    }
+  }
+  if (pair >= sh.pairs) return;
+  double* out = a.partial + (size_t)(a.part0 + blockIdx.x) * (L + 1) * nb * nb;
+  float* s_red = s_red_all + warp * 32 * 17;
+  con_flush(sh, acc_a, la, tile, g, B1, B2, nb, L, out, s_red, lane);
+  if (lb != la) con_flush(sh, acc_b, lb, tile, g, B1, B2, nb, L, out, s_red, lane);
+}
+
+// Resident blocks per SM of the contraction for this shape (0 if it cannot run).
+int contract_fp32_blocks_per_sm(int nbins, int lmax, int row) {
+  const ConShape sh = con_shape(nbins, lmax, row);
+  const size_t smem = (size_t)sh.smem_floats * sizeof(float);
+  if (smem > 200 * 1024) return 0;
+  if (cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_contract_fp32, sh.threads, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
 cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t st) {
-  const int E = (a.lmax + 1) * a.nbins * (a.nbins + 1) / 2;
-  const int groups = (E + kConGroup - 1) / kConGroup;
   if (a.np == 0) return cudaSuccess;
-  const int srowsz = a.nbins * (a.row + 1);
-  const int rows_cap = srowsz > kConSmemFloats ? srowsz : kConSmemFloats;
-  const size_t smem = (size_t)rows_cap * sizeof(float);
+  const ConShape sh = con_shape(a.nbins, a.lmax, a.row);
+  const size_t smem = (size_t)sh.smem_floats * sizeof(float);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_contract_fp32<<<dim3(nparts, groups), kConThreads, smem, st>>>(a);
+  k_contract_fp32<<<dim3(nparts, sh.ny), sh.threads, smem, st>>>(a);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -152,6 +223,36 @@ cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbi
   const int total = (lmax + 1) * nbins * nbins;
   const int blocks = (total + 255) / 256;
   k_finalize<<<blocks, 256, 0, st>>>(partial, nparts, lmax, nbins, zeta);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// Weighted pair sums of the two-point function from the same pass:
+// sum_p w_p sum_{j in b} w_j = sqrt(4 pi) sum_p w_p a_00(p, b), the a_00 column
+// of the M rows (col).  Block bx takes a fixed slice of the primaries, four
+// thread groups interleave over it, and the groups are added in a fixed order
+// to partial[bx][b] (FP64; accumulated over the chunks of one compute).
+__global__ void __launch_bounds__(256) k_pair_sums(const float* __restrict__ M, const float* __restrict__ w,
+                                                   int64_t np, int nbins, int row, int col,
+                                                   double* __restrict__ partial) {
+  __shared__ double s[4][kNbinsCap];
+  const int64_t nparts = gridDim.x, bx = blockIdx.x;
+  const int64_t p0 = np * bx / nparts, p1 = np * (bx + 1) / nparts;
+  const int g = threadIdx.x >> 6, b = threadIdx.x & 63;
+  double acc = 0.0;
+  if (b < nbins)
+    for (int64_t p = p0 + g; p < p1; p += 4) acc += (double)w[p] * (double)M[(p * nbins + b) * row + col];
+  s[g][b] = acc;
+  __syncthreads();
+  if (threadIdx.x < nbins) {
+    const int bb = threadIdx.x;
+    partial[bx * nbins + bb] += (s[0][bb] + s[1][bb]) + (s[2][bb] + s[3][bb]);
+  }
+}
+
+cudaError_t launch_pair_sums(const float* M, const float* w, int64_t np, int nbins, int row, int col,
+                             double* partial, int nparts, cudaStream_t st) {
+  k_pair_sums<<<nparts, 256, 0, st>>>(M, w, np, nbins, row, col, partial);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -49,6 +49,8 @@ struct TcArgs {
   unsigned int ktiles[kLmaxCap + 1];  // 128-byte K tiles per l
   double* partial;                    // [nl][nsplit][nbins][nbins]
   unsigned int* err;                  // bit 0: a bounded wait timed out
+  long long timeout_cycles;           // limit of every mbarrier wait
+  int inject_stall;                   // test hook: the MMA thread first waits on a barrier nothing signals
 };
 
 // ---------------------------------------------------------------------------
@@ -82,11 +84,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Wait for the phase of `bar` with parity `parity`; false if this CTA has
 // given up (timeout here or elsewhere in the CTA).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, unsigned int* err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, unsigned int* err,
+                                          long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kTcTimeoutCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicOr(err, 1u);
       return false;
@@ -190,7 +193,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
   uint64_t* accfull = empty + S;
   uint64_t* accempty = accfull + 2;
   uint64_t* done = accempty + 2;
-  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* never = done + 1;  // no thread ever arrives here (fault-injection hook)
+  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* s_abort = reinterpret_cast<volatile int*>(s_taddr + 1);
 
   if (threadIdx.x == 0) {
@@ -203,6 +207,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
       mbar_init(accempty + b, 128);
     }
     mbar_init(done, 1);
+    mbar_init(never, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
       for (uint32_t it = 0; it < ntiles; ++it) {
         const int s = (int)(it % S);
         const uint32_t ph = (it / S) & 1u;
-        if (!mbar_wait(empty + s, ph ^ 1u, s_abort, a.err)) break;
+        if (!mbar_wait(empty + s, ph ^ 1u, s_abort, a.err, a.timeout_cycles)) break;
         uint8_t* st = sm + (size_t)s * STAGE;
         mbar_expect_tx(full + s, STAGE);
         const int x = (int)((t0 + it) * (TF32 ? 32u : 64u));
@@ -236,13 +241,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
         if (!TF32) tma_load_2d(st + NA * A_BYTES + B_BYTES, &maps.m[l][3], x, 0, full + s);
         ++issued;
       }
-      if (*s_abort) {
-        // bounded wait for this CTA's copies still in flight
-        const uint32_t first = issued > (uint32_t)S ? issued - S : 0;
-        for (uint32_t it = first; it < issued; ++it) {
-          const long long tw = clock64();
-          while (!mbar_try_wait(full + (it % S), (it / S) & 1u) && clock64() - tw < kTcTimeoutCycles) {
-          }
+      // bounded wait for this CTA's copies still in flight (the consumer may
+      // give up later than this loop ends); on the normal path these phases
+      // have completed and each test passes at once
+      const uint32_t first = issued > (uint32_t)S ? issued - S : 0;
+      for (uint32_t it = first; it < issued; ++it) {
+        const long long tw = clock64();
+        while (!mbar_try_wait(full + (it % S), (it / S) & 1u) && clock64() - tw < a.timeout_cycles) {
         }
       }
     }
@@ -250,14 +255,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
     // ---- MMA issuer
     if (lane == 0) {
       const uint32_t idesc = make_idesc(TF32, a.npad);
-      for (uint32_t it = 0; it < ntiles; ++it) {
+      // fault injection: a wait that runs out, then the ordinary abort path
+      const bool go = !a.inject_stall || mbar_wait(never, 0, s_abort, a.err, a.timeout_cycles);
+      for (uint32_t it = 0; go && it < ntiles; ++it) {
         const int s = (int)(it % S);
         const uint32_t ph = (it / S) & 1u;
         const uint32_t f = it / kTcFlushTiles;
         const uint32_t buf = f & 1u;
         const bool first_of_flush = (it % kTcFlushTiles) == 0;
-        if (first_of_flush && f >= 2 && !mbar_wait(accempty + buf, ((f >> 1) - 1) & 1u, s_abort, a.err)) break;
-        if (!mbar_wait(full + s, ph, s_abort, a.err)) break;
+        if (first_of_flush && f >= 2 && !mbar_wait(accempty + buf, ((f >> 1) - 1) & 1u, s_abort, a.err, a.timeout_cycles)) break;
+        if (!mbar_wait(full + s, ph, s_abort, a.err, a.timeout_cycles)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(sm + (size_t)s * STAGE);
         const uint32_t a_hi = sa, a_lo = sa + A_BYTES;
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
       // all MMAs issued by this thread complete before TMEM is released
       tc_commit(done);
       const long long tw = clock64();
-      while (!mbar_try_wait(done, 0) && clock64() - tw < kTcTimeoutCycles) {
+      while (!mbar_try_wait(done, 0) && clock64() - tw < a.timeout_cycles) {
       }
     }
   } else {
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
     const uint32_t row_addr = taddr + ((uint32_t)(warp * 32) << 16);
     for (uint32_t f = 0; f < nflush; ++f) {
       const uint32_t buf = f & 1u;
-      if (!mbar_wait(accfull + buf, (f >> 1) & 1u, s_abort, a.err)) break;
+      if (!mbar_wait(accfull + buf, (f >> 1) & 1u, s_abort, a.err, a.timeout_cycles)) break;
       tc_fence_after();
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -433,7 +440,8 @@ cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t n
 
 cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const unsigned long long* h_lbase,
                                const unsigned long long* h_kp, void* ahi, void* alo, void* bhi, void* blo,
-                               double* partial, int nsplit, unsigned int* err, cudaStream_t st) {
+                               double* partial, int nsplit, unsigned int* err, bool inject_stall,
+                               cudaStream_t st) {
   if (np == 0) return cudaSuccess;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -449,6 +457,9 @@ cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const
   a.nsplit = nsplit;
   a.partial = partial;
   a.err = err;
+  // about 2 s per wait; an injected stall gives up after about 10 ms
+  a.timeout_cycles = inject_stall ? 20000000ll : kTcTimeoutCycles;
+  a.inject_stall = inject_stall ? 1 : 0;
   void* bases[4] = {ahi, alo, bhi, blo};
   for (int l = 0; l <= lmax; ++l) {
     a.ktiles[l] = (unsigned int)(h_kp[l] / (tf32 ? 32 : 64));

@@ -21,6 +21,8 @@
 namespace ctb {
 
 constexpr int kLmaxCap = CTB_LMAX_CAP;
+// bytes allocated past the last neighbour-list entry (read by L2 prefetches only)
+constexpr size_t kListSlackBytes = 1024;
 constexpr int kNbinsCap = CTB_NBINS_CAP;
 constexpr int kWarp = 32;
 // coefficients accumulated per pass of the pair kernel (register budget)
@@ -43,6 +45,29 @@ struct Geom {
   float rcell;         // r_max in cell units, padded by a small slack
   float cell_scale;    // nc / 2^shift : units -> cell units
 };
+
+// Rows of the neighbour scan: W x W x-rows of cells at (dy, dz) offsets
+// off0 .. off0 + W - 1 around the primary's cell, or the whole periodic cube
+// when that window would wrap onto itself.  The scan takes the rows in blocks
+// of 32 (one per lane).
+struct RowWindow {
+  int W, off0;
+  bool fullwin;
+};
+__host__ __device__ inline RowWindow row_window(const Geom& g) {
+  const int K = (int)floorf(g.rcell) + 1;
+  RowWindow w{2 * K + 1, -K, false};
+  if (g.periodic && w.W >= (int)g.nc) {
+    w.W = (int)g.nc;
+    w.off0 = -(((int)g.nc - 1) / 2);
+    w.fullwin = true;
+  }
+  return w;
+}
+__host__ __device__ inline int row_blocks(const Geom& g) {
+  const RowWindow w = row_window(g);
+  return (w.W * w.W + 31) / 32;
+}
 
 // ---------------------------------------------------------------------------
 // real-harmonic coefficient layout of one pair-kernel configuration
@@ -69,6 +94,10 @@ __host__ __device__ constexpr int pass_end(int L, int m0, int cap) {
   }
   return m - 1;
 }
+
+// accumulator slots of the m-range pass of the pair kernel for ell_max L that
+// starts at column m0
+__host__ __device__ constexpr int pass_cap(int L, int m0) { return (void)L, (void)m0, kPassCap; }
 
 __host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
 
@@ -177,6 +206,10 @@ struct StreamArgs {
   unsigned long long* work;       // work counter (zeroed before launch)
   unsigned long long* total;      // binned pairs of this launch (count pass, accumulated)
   const uint32_t* keys;           // sorted cell keys of a batch (catalogue = key / ncells), or NULL
+  uint8_t* codes;                 // bin code per candidate (written: count, read: fill)
+  unsigned long long code_cap;    // bytes of codes
+  unsigned long long* code_total; // code bytes of this launch (count pass; the range allocator)
+  unsigned long long* code_base;  // [prim_count][row_blocks] start of each row block's codes
   Geom g;
 };
 int stream_blocks_per_sm(bool fill, int nbins);
@@ -217,6 +250,15 @@ struct ContractArgs {
   int part0;               // first partial row this launch writes
 };
 cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t st);
+int contract_fp32_blocks_per_sm(int nbins, int lmax, int row);
+
+// edge.cu
+void make_threej_table(int lmax, std::vector<double>& t);  // (a b c; 0 0 0)^2, [a][b][c], a,b,c <= lmax
+cudaError_t launch_edge_correct(const double* zn, const double* zr, const double* tj, int lmax, int nbins,
+                                double* out, cudaStream_t st);
+// partial[part][b] += sum over a fixed slice of the primaries of w_p * M[p][b][col]
+cudaError_t launch_pair_sums(const float* M, const float* w, int64_t np, int nbins, int row, int col,
+                             double* partial, int nparts, cudaStream_t st);
 cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbins,
                             double* zeta, cudaStream_t st);
 
@@ -229,7 +271,8 @@ cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t n
                         void* ahi, void* alo, void* bhi, void* blo, cudaStream_t st);
 cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const unsigned long long* h_lbase,
                                const unsigned long long* h_kp, void* ahi, void* alo, void* bhi, void* blo,
-                               double* partial, int nsplit, unsigned int* err, cudaStream_t st);
+                               double* partial, int nsplit, unsigned int* err, bool inject_stall,
+                               cudaStream_t st);
 cudaError_t launch_finalize_tc(const double* partial, int lmax, int nsplit, int nbins, double* zeta,
                                cudaStream_t st);
 

@@ -31,7 +31,9 @@ namespace ctb {
 
 constexpr uint32_t kNone = 0xffffffffu;
 // The list words of one primary are one contiguous range; the read position
-// is kept this many 128-byte lines ahead of use in L2.
+// is kept this many 128-byte lines ahead of use in L2.  The list buffer is
+// allocated with kListSlackBytes past its last entry for prefetches that run
+// beyond it.
 constexpr uint32_t kListPrefetchLines = 6;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -237,7 +239,41 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
   // the second record word: the previous run could not see past this run
   // when it is a single step long, so take it from (cur, nxt)
   pf.j1 = rec_at(lists, cur, nxt, T, 1, lane);
-  for (uint32_t t = 0; t < T; ++t) {
+  uint32_t t = 0;
+  // Steps whose lanes all hold a neighbour and whose look-ahead words are in
+  // this run: no validity tests, no run switch.  (The list buffer has slack
+  // past its last entry, so the L2 prefetch needs no bound here.)
+  {
+    const uint32_t full = cur.n >> 5;
+    if (t + 3u < full) {
+      // two gathers in flight: q0 = point(t), q1 = point(t + 1), j1 = word(t + 2)
+      uint4 q1 = __ldg(pts + pf.j1);
+      pf.j1 = __ldcg(lists + cur.off + 64u + (uint32_t)lane);
+      const uint32_t* __restrict__ wp = lists + cur.off + 96u + (uint32_t)lane;
+      const uint32_t* pp = lists + cur.off + kListPrefetchLines * 32u;
+      const bool lane0 = lane == 0;
+#pragma unroll 1
+      for (; t + 3u < full; ++t) {
+        if (lane0) prefetch_l2(pp);
+        pp += 32;
+        const uint4 q = pf.q0;
+        pf.q0 = q1;
+        q1 = __ldg(pts + pf.j1);
+        pf.j1 = __ldcg(wp);
+        wp += 32;
+        const float dx = __int2float_rn((int)(q.x - P.x));
+        const float dy = __int2float_rn((int)(q.y - P.y));
+        const float dz = __int2float_rn((int)(q.z - P.z));
+        const float ir = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        accum_pass<L, M0, M1>(a, acc, __uint_as_float(q.w), dx * ir, dy * ir, dz * ir);
+      }
+      // back to one gather in flight: q0 = point(t) (valid), j1 = word(t + 1)
+      pf.j0 = 0u;
+      pf.j1 = rec_at(lists, cur, nxt, T, t + 1, lane);
+    }
+  }
+  // the last steps of the run: partial lanes, look-ahead into the next run
+  for (; t < T; ++t) {
     const uint32_t pa = cur.off + (t + kListPrefetchLines) * 32u;
     if (lane == 0 && pa < pe) prefetch_l2(lists + pa);
     const uint4 q = pf.q0;
@@ -288,7 +324,7 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
 // The m-range passes of one bin; the last pass prefetches the next bin's run.
 template <int L, int M0, int BASE>
 struct PassChain {
-  static constexpr int M1 = pass_end(L, M0, kPassCap);
+  static constexpr int M1 = pass_end(L, M0, pass_cap(L, M0));
   static constexpr int NCP = round32(coef_count(L, M0, M1));
   static constexpr bool LAST = M1 + 1 > L;
   __device__ static __forceinline__ void run(const AlmArgs& a, Run cur, Run nxt_bin, const uint4 P, Prefetch& pf,
@@ -302,13 +338,16 @@ struct PassChain {
 __host__ __device__ constexpr int max_ncp(int L) {
   int best = 0;
   for (int m0 = 0; m0 <= L;) {
-    int m1 = pass_end(L, m0, kPassCap);
+    int m1 = pass_end(L, m0, pass_cap(L, m0));
     int v = round32(coef_count(L, m0, m1));
     if (v > best) best = v;
     m0 = m1 + 1;
   }
   return best;
 }
+
+// resident blocks of 4 warps the register budget is sized for
+__host__ __device__ constexpr int alm_min_blocks(int L) { return max_ncp(L) <= 64 ? 5 : (max_ncp(L) <= 96 ? 4 : 3); }
 
 template <int L>
 constexpr size_t alm_smem_per_warp() {
@@ -319,7 +358,7 @@ constexpr size_t alm_smem_per_warp() {
 // lists buffer; each list is accumulated in registers and flushed once, with
 // the next list's first loads already in flight.
 template <int L>
-__global__ void __launch_bounds__(128, 3) k_alm(AlmArgs a) {
+__global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
   extern __shared__ float s_alm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;

@@ -21,7 +21,7 @@ void make_layout(int L, Layout* out) {
   int base = 0;
   for (int i = 0; i < (kLmaxCap + 1) * (kLmaxCap + 1); ++i) y.slot[i] = -1;
   for (int m0 = 0; m0 <= L;) {
-    int m1 = pass_end(L, m0, kPassCap);
+    int m1 = pass_end(L, m0, pass_cap(L, m0));
     int ncp = round32(coef_count(L, m0, m1));
     y.m0[y.npass] = m0;
     y.m1[y.npass] = m1;

@@ -11,9 +11,14 @@
 //
 // Two passes per chunk of primaries:
 //   count: pairs per (primary, bin)  -> counts (then an exclusive scan on the
-//          host stream gives each (primary, bin) list its start)
-//   fill:  each pair's neighbour index written into its (primary, bin) list,
-//          in stream order (match_any ranks lanes that share a bin)
+//          host stream gives each (primary, bin) list its start); the bin of
+//          every candidate is also stored as one byte (kNoBin: not a pair):
+//          each block of 32 rows takes a range of its warp's pool in the code
+//          buffer, and each cell-row segment in it starts on a 4-byte boundary
+//   fill:  walks the same candidate stream, reads the stored bin codes four
+//          per lane (no point loads, no distances) and writes each pair's
+//          neighbour index into its (primary, bin) list (match_any ranks the
+//          lanes that share a bin)
 // The kernel holds few registers, so many warps per SM hide the load latency
 // that dominates this phase.
 #include "ctb_internal.cuh"
@@ -29,6 +34,78 @@ __device__ __forceinline__ int pmod(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
+constexpr uint8_t kNoBin = 0xff;  // bin code of a candidate that is not a pair
+constexpr unsigned long long kCodePool = 16384;  // code bytes a warp takes at a time
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Geometry of one primary's row window, shared by both passes.
+struct RowWin {
+  int W, off0, nrows;
+  bool fullwin;
+  float R2, fx, fry, frz;  // (r_max in cell units)^2, primary's position in cell units
+  int cxp, cyp, czp;
+  uint32_t cbase;
+};
+
+// The point ranges of row t of the window (up to two: periodic wrap in x);
+// empty ranges have s >= e.
+__device__ __forceinline__ void row_ranges(const StreamArgs& a, const Geom& g, const RowWin& rw, int t, uint32_t& s0,
+                                           uint32_t& e0, uint32_t& s1, uint32_t& e1) {
+  const uint32_t nc = g.nc;
+  s0 = e0 = s1 = e1 = 0;
+  if (t >= rw.nrows) return;
+  const int dy = t % rw.W + rw.off0, dz = t / rw.W + rw.off0;
+  float gy = slab_dist(dy, rw.fry), gz = slab_dist(dz, rw.frz);
+  if (rw.fullwin) {
+    gy = fminf(gy, fminf(slab_dist(dy - (int)nc, rw.fry), slab_dist(dy + (int)nc, rw.fry)));
+    gz = fminf(gz, fminf(slab_dist(dz - (int)nc, rw.frz), slab_dist(dz + (int)nc, rw.frz)));
+  }
+  const float rho2 = gy * gy + gz * gz;
+  int cy = rw.cyp + dy, cz = rw.czp + dz;
+  bool ok = rho2 < rw.R2;
+  if (g.periodic) {
+    cy = pmod(cy, (int)nc);
+    cz = pmod(cz, (int)nc);
+  } else {
+    ok = ok && cy >= 0 && cy < (int)nc && cz >= 0 && cz < (int)nc;
+  }
+  if (!ok) return;
+  const float hw = sqrtf(rw.R2 - rho2);
+  int lo = (int)floorf(rw.fx - hw), hi = (int)floorf(rw.fx + hw);
+  const uint32_t rb = rw.cbase + ((uint32_t)cz * nc + (uint32_t)cy) * nc;
+  int a0 = 1, b0 = 0, a1 = 1, b1 = 0;
+  if (g.periodic) {
+    if (hi - lo + 1 >= (int)nc) {
+      a0 = 0;
+      b0 = (int)nc - 1;
+    } else {
+      const int lm = pmod(lo, (int)nc), hm = pmod(hi, (int)nc);
+      a0 = lm;
+      if (lm <= hm) {
+        b0 = hm;
+      } else {
+        b0 = (int)nc - 1;
+        a1 = 0;
+        b1 = hm;
+      }
+    }
+  } else {
+    a0 = max(lo, 0);
+    b0 = min(hi, (int)nc - 1);
+  }
+  if (a0 <= b0) {
+    s0 = __ldg(a.cell_start + rb + a0);
+    e0 = __ldg(a.cell_start + rb + b0 + 1);
+  }
+  if (a1 <= b1) {
+    s1 = __ldg(a.cell_start + rb + a1);
+    e1 = __ldg(a.cell_start + rb + b1 + 1);
+  }
+}
+
 template <bool FILL>
 __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
   extern __shared__ uint32_t s_cnt_all[];
@@ -40,19 +117,22 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
   uint32_t* cnt = s_cnt_all + warp * (FILL ? kNbinsCap : nbins * 32);
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t nc = g.nc;
-  const float R2 = g.rcell * g.rcell;
-  const int K = (int)floorf(g.rcell) + 1;
-  int W = 2 * K + 1, off0 = -K;
-  bool fullwin = false;
-  if (g.periodic && W >= (int)nc) {
-    W = (int)nc;
-    off0 = -(((int)nc - 1) / 2);
-    fullwin = true;
+  RowWin rw;
+  rw.R2 = g.rcell * g.rcell;
+  {
+    const RowWindow win = row_window(g);
+    rw.W = win.W;
+    rw.off0 = win.off0;
+    rw.fullwin = win.fullwin;
   }
-  const int nrows = W * W;
+  rw.nrows = rw.W * rw.W;
+  const int nrb = (rw.nrows + 31) / 32;
   const uint64_t lowmask = (1ull << g.shift) - 1ull;
   const float frac_scale = 1.0f / (float)(1ull << g.shift);
   unsigned long long my_pairs = 0;
+  // count: this warp's pool in the code buffer (row blocks take consecutive
+  // ranges of it; a new pool is taken when one does not fit)
+  unsigned long long pool = 0, pool_end = 0;
 
   while (true) {
     unsigned long long i = 0;
@@ -63,7 +143,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
     const uint32_t sp = a.prim ? __ldg(a.prim + gi) : (uint32_t)gi;
     const uint4 P = __ldg(a.pts + sp);
     // batch: the primary's catalogue owns cells [cat * ncells, (cat + 1) * ncells)
-    const uint32_t cbase = a.keys ? (__ldg(a.keys + sp) / g.ncells) * g.ncells : 0u;
+    rw.cbase = a.keys ? (__ldg(a.keys + sp) / g.ncells) * g.ncells : 0u;
     if (!FILL && lane == 0) a.wprim[i] = __uint_as_float(P.w);
     const uint64_t ib = i * (uint64_t)nbins;
     if (FILL) {
@@ -74,64 +154,41 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
     __syncwarp();
 
     const uint64_t sx = (uint64_t)P.x * nc, sy = (uint64_t)P.y * nc, sz = (uint64_t)P.z * nc;
-    const int cxp = (int)(sx >> g.shift), cyp = (int)(sy >> g.shift), czp = (int)(sz >> g.shift);
-    const float fry = (float)(sy & lowmask) * frac_scale;
-    const float frz = (float)(sz & lowmask) * frac_scale;
-    const float fx = (float)cxp + (float)(sx & lowmask) * frac_scale;
+    rw.cxp = (int)(sx >> g.shift);
+    rw.cyp = (int)(sy >> g.shift);
+    rw.czp = (int)(sz >> g.shift);
+    rw.fry = (float)(sy & lowmask) * frac_scale;
+    rw.frz = (float)(sz & lowmask) * frac_scale;
+    rw.fx = (float)rw.cxp + (float)(sx & lowmask) * frac_scale;
 
-    for (int t0 = 0; t0 < nrows; t0 += 32) {
-      // ---- this lane's row: up to two point ranges (periodic wrap in x)
-      const int t = t0 + lane;
-      uint32_t s0 = 0, e0 = 0, s1 = 0, e1 = 0;
-      if (t < nrows) {
-        const int dy = t % W + off0, dz = t / W + off0;
-        float gy = slab_dist(dy, fry), gz = slab_dist(dz, frz);
-        if (fullwin) {
-          gy = fminf(gy, fminf(slab_dist(dy - (int)nc, fry), slab_dist(dy + (int)nc, fry)));
-          gz = fminf(gz, fminf(slab_dist(dz - (int)nc, frz), slab_dist(dz + (int)nc, frz)));
+    for (int t0 = 0, rb = 0; t0 < rw.nrows; t0 += 32, ++rb) {
+      uint32_t s0, e0, s1, e1;
+      row_ranges(a, g, rw, t0 + lane, s0, e0, s1, e1);
+      // this row block's range of the code buffer: its segments in the order
+      // below, each padded to a multiple of 4 codes
+      unsigned long long span = (s0 < e0 ? (e0 - s0 + 3u) & ~3u : 0u) + (s1 < e1 ? (e1 - s1 + 3u) & ~3u : 0u);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) span += __shfl_xor_sync(0xffffffffu, span, o);
+      unsigned long long pos = 0;
+      bool codes_ok = true;
+      if (FILL) {
+        pos = __ldg(a.code_base + i * (uint64_t)nrb + rb);
+        // the block's codes to L2 ahead of the segment loads (one line per lane)
+        for (unsigned long long ln = (unsigned long long)lane * 128u; ln < span; ln += 32u * 128u)
+          prefetch_l2(a.codes + pos + ln);
+      } else {
+        if (pool + span > pool_end) {
+          const unsigned long long take = span > kCodePool ? span : kCodePool;
+          if (lane == 0) pool = atomicAdd(a.code_total, take);
+          pool = __shfl_sync(0xffffffffu, pool, 0);
+          pool_end = pool + take;
         }
-        const float rho2 = gy * gy + gz * gz;
-        int cy = cyp + dy, cz = czp + dz;
-        bool ok = rho2 < R2;
-        if (g.periodic) {
-          cy = pmod(cy, (int)nc);
-          cz = pmod(cz, (int)nc);
-        } else {
-          ok = ok && cy >= 0 && cy < (int)nc && cz >= 0 && cz < (int)nc;
-        }
-        if (ok) {
-          const float hw = sqrtf(R2 - rho2);
-          int lo = (int)floorf(fx - hw), hi = (int)floorf(fx + hw);
-          const uint32_t rb = cbase + ((uint32_t)cz * nc + (uint32_t)cy) * nc;
-          int a0 = 1, b0 = 0, a1 = 1, b1 = 0;
-          if (g.periodic) {
-            if (hi - lo + 1 >= (int)nc) {
-              a0 = 0;
-              b0 = (int)nc - 1;
-            } else {
-              const int lm = pmod(lo, (int)nc), hm = pmod(hi, (int)nc);
-              a0 = lm;
-              if (lm <= hm) {
-                b0 = hm;
-              } else {
-                b0 = (int)nc - 1;
-                a1 = 0;
-                b1 = hm;
-              }
-            }
-          } else {
-            a0 = max(lo, 0);
-            b0 = min(hi, (int)nc - 1);
-          }
-          if (a0 <= b0) {
-            s0 = __ldg(a.cell_start + rb + a0);
-            e0 = __ldg(a.cell_start + rb + b0 + 1);
-          }
-          if (a1 <= b1) {
-            s1 = __ldg(a.cell_start + rb + a1);
-            e1 = __ldg(a.cell_start + rb + b1 + 1);
-          }
-        }
+        pos = pool;
+        pool += span;
+        if (lane == 0) a.code_base[i * (uint64_t)nrb + rb] = pos;
+        // past the buffer: counts stay exact, codes are dropped and the host
+        // grows the buffer and counts the chunk again
+        codes_ok = pos + span <= a.code_cap;
       }
       unsigned pend = __ballot_sync(0xffffffffu, s0 < e0 || s1 < e1);
       while (pend) {
@@ -145,46 +202,62 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
           else s1 = e1;
         }
         pend = __ballot_sync(0xffffffffu, s0 < e0 || s1 < e1);
-        for (uint32_t base = cs; base < ce; base += 32) {
-          const uint32_t j = base + lane;
-          const bool valid = j < ce;
-          const uint4 q = valid ? __ldg(a.pts + j) : P;
-          const int ix = (int)(q.x - P.x), iy = (int)(q.y - P.y), iz = (int)(q.z - P.z);
-          const float dx = __int2float_rn(ix), dy = __int2float_rn(iy), dz = __int2float_rn(iz);
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          bool inb = valid && r2 > 0.f && r2 >= g.rlo2_u && r2 < g.rhi2_u;
-          int b = 0;
-          if (inb) {
-            const float r = r2 * rsqrtf(r2);
-            const float tt = (r - g.rmin_u) * g.inv_dr_u;
-            b = (int)floorf(tt);
-            const float fr = tt - (float)b;
-            if (b < 0 || b >= nbins || fr < 1e-4f || fr > 1.f - 1e-4f) {
-              // within float rounding of an edge: exact integer r^2 vs exact thresholds
-              const unsigned long long e2 = (unsigned long long)((long long)ix * ix + (long long)iy * iy +
-                                                                 (long long)iz * iz);
-              if (e2 == 0ull || e2 < __ldg(a.thr) || e2 >= __ldg(a.thr + nbins)) {
-                inb = false;
-              } else {
-                b = min(max(b, 0), nbins - 1);
-                while (e2 < __ldg(a.thr + b)) --b;
-                while (e2 >= __ldg(a.thr + b + 1)) ++b;
+        const unsigned long long seg0 = pos;  // code of candidate j: codes[seg0 + (j - cs)]
+        pos += (ce - cs + 3u) & ~3u;
+        if (FILL) {
+          // 128 candidates per step: lane l takes candidates 4l .. 4l+3 of it
+          const uint32_t* segw = reinterpret_cast<const uint32_t*>(a.codes + seg0);
+          for (uint32_t base = cs; base < ce; base += 128) {
+            const uint32_t j4 = base + 4u * (uint32_t)lane;
+            const uint32_t word = j4 < ce ? segw[(j4 - cs) >> 2] : 0xffffffffu;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t j = j4 + (uint32_t)k;
+              const uint32_t code = (word >> (8 * k)) & 0xffu;
+              const bool inb = j < ce && code != kNoBin;
+              const int b = (int)code;
+              const unsigned act = __ballot_sync(0xffffffffu, inb);
+              if (inb) {
+                const unsigned grp = __match_any_sync(act, b);
+                const unsigned rank = __popc(grp & lt);
+                const uint32_t c0 = cnt[b];
+                __syncwarp(act);
+                a.lists[(uint64_t)c0 + rank] = j;
+                if (rank == 0) cnt[b] = c0 + __popc(grp);
               }
+              __syncwarp();
             }
           }
-          if (FILL) {
-            const unsigned act = __ballot_sync(0xffffffffu, inb);
+        } else {
+          for (uint32_t base = cs; base < ce; base += 32) {
+            const uint32_t j = base + lane;
+            const bool valid = j < ce;
+            const uint4 q = valid ? __ldg(a.pts + j) : P;
+            const int ix = (int)(q.x - P.x), iy = (int)(q.y - P.y), iz = (int)(q.z - P.z);
+            const float dx = __int2float_rn(ix), dy = __int2float_rn(iy), dz = __int2float_rn(iz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool inb = valid && r2 > 0.f && r2 >= g.rlo2_u && r2 < g.rhi2_u;
+            int b = 0;
             if (inb) {
-              const unsigned grp = __match_any_sync(act, b);
-              const unsigned rank = __popc(grp & lt);
-              const uint32_t c0 = cnt[b];
-              __syncwarp(act);
-              a.lists[(uint64_t)c0 + rank] = j;
-              if (rank == 0) cnt[b] = c0 + __popc(grp);
+              const float r = r2 * rsqrtf(r2);
+              const float tt = (r - g.rmin_u) * g.inv_dr_u;
+              b = (int)floorf(tt);
+              const float fr = tt - (float)b;
+              if (b < 0 || b >= nbins || fr < 1e-4f || fr > 1.f - 1e-4f) {
+                // within float rounding of an edge: exact integer r^2 vs exact thresholds
+                const unsigned long long e2 = (unsigned long long)((long long)ix * ix + (long long)iy * iy +
+                                                                   (long long)iz * iz);
+                if (e2 == 0ull || e2 < __ldg(a.thr) || e2 >= __ldg(a.thr + nbins)) {
+                  inb = false;
+                } else {
+                  b = min(max(b, 0), nbins - 1);
+                  while (e2 < __ldg(a.thr + b)) --b;
+                  while (e2 >= __ldg(a.thr + b + 1)) ++b;
+                }
+              }
             }
-            __syncwarp();
-          } else if (inb) {
-            cnt[b * 32 + lane] += 1u;  // lane-private: no ordering, no conflict
+            if (valid && codes_ok) a.codes[seg0 + (j - cs)] = inb ? (uint8_t)b : kNoBin;
+            if (inb) cnt[b * 32 + lane] += 1u;  // lane-private: no ordering, no conflict
           }
         }
       }

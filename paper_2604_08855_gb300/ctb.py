@@ -22,16 +22,17 @@ LIB_PATH = os.path.join(_HERE, "_build", "libctb.so")
 
 OK = 0
 ERR_ARG, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
-OPT_PRECISION, OPT_CELLS_PER_RMAX, OPT_BIN_CAPACITY, OPT_WARPS_PER_BLOCK, OPT_CHUNK_PRIMARIES, \
-    OPT_DETERMINISTIC = 1, 2, 3, 4, 5, 6
+OPT_PRECISION, OPT_CELLS_PER_RMAX, OPT_LIST_CAPACITY, OPT_WARPS_PER_BLOCK, OPT_CHUNK_PRIMARIES, \
+    OPT_DETERMINISTIC, OPT_AUTOTUNE, OPT_FAULT_INJECT = 1, 2, 3, 4, 5, 6, 7, 8
+INJECT_STALL, INJECT_ALLOC = 1, 2
 PREC_FP32, PREC_BF16X3, PREC_TF32 = 0, 1, 2
 LMAX_CAP, NBINS_CAP = 20, 64
 
 # every symbol include/ctb.h declares
 EXPORTS = ("ctb_create", "ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm",
            "ctb_compute_batch", "ctb_set_option", "ctb_set_stream", "ctb_set_allocator",
-           "ctb_get_timings", "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_launch_count", "ctb_contract_noalloc",
-           "ctb_destroy", "ctb_last_error", "ctb_version")
+           "ctb_get_timings", "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_grid",
+           "ctb_get_2pcf", "ctb_edge_correct", "ctb_get_launch_count", "ctb_contract_noalloc", "ctb_destroy", "ctb_last_error", "ctb_version")
 
 _lib = None
 
@@ -65,6 +66,9 @@ def load(path: str | None = None):
     lib.ctb_get_timings.argtypes = [vp, vp, i32]
     lib.ctb_get_pair_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.ctb_get_chunk_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.ctb_get_grid.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.ctb_get_2pcf.argtypes = [vp, vp, i32]
+    lib.ctb_edge_correct.argtypes = [vp, vp, vp, vp]
     lib.ctb_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.ctb_contract_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     lib.ctb_destroy.argtypes = [vp]
@@ -75,7 +79,8 @@ def load(path: str | None = None):
     lib.ctb_version.restype = ctypes.c_char_p
     for name in ("ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm", "ctb_compute_batch",
                  "ctb_set_option", "ctb_set_stream", "ctb_set_allocator", "ctb_get_timings",
-                 "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_launch_count", "ctb_contract_noalloc"):
+                 "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_grid", "ctb_get_2pcf",
+                 "ctb_edge_correct", "ctb_get_launch_count", "ctb_contract_noalloc"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -231,6 +236,34 @@ class CTB:
         v = ctypes.c_uint64(0)
         self._check(self.lib.ctb_get_pair_count(self._h, ctypes.byref(v)))
         return int(v.value)
+
+    def edge_correct(self, zeta_nnn, zeta_rrr, out=None):
+        """Edge-corrected Legendre coefficients from a data-minus-randoms zeta
+        and the randoms' zeta (numpy or torch, host or device)."""
+        zn, zr = _as_f64(zeta_nnn), _as_f64(zeta_rrr)
+        for z in (zn, zr):
+            if tuple(z.shape) != self.zeta_shape:
+                raise CTBError(ERR_ARG, f"zeta shape {tuple(z.shape)} != {self.zeta_shape}")
+        o = self._out(out, self.zeta_shape, np.float64)
+        self._check(self.lib.ctb_edge_correct(self._h, _ptr(zn), _ptr(zr), _ptr(o)))
+        return o
+
+    def pair_sums(self, catalogues: int = 1) -> np.ndarray:
+        """Weighted pair sums sum_p w_p sum_{j in b} w_j of the last compute
+        ([nbins]), or of each catalogue of the last batch ([k, nbins])."""
+        out = np.zeros((catalogues, self.nbins), dtype=np.float64)
+        r = self.lib.ctb_get_2pcf(self._h, out.ctypes.data_as(ctypes.c_void_p), out.size)
+        if r < 0:
+            self._check(r)
+        if r != out.size:
+            raise CTBError(ERR_ARG, f"{r // self.nbins} catalogues hold pair sums, asked for {catalogues}")
+        return out[0] if catalogues == 1 else out
+
+    def grid(self) -> tuple[int, int]:
+        """(cells per r_max, cells per axis) of the current catalogue's grid."""
+        k, nc = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self.lib.ctb_get_grid(self._h, ctypes.byref(k), ctypes.byref(nc)))
+        return int(k.value), int(nc.value)
 
     def chunk_count(self) -> int:
         """Primary chunks (launches of each pair kernel) of the last compute."""

@@ -15,6 +15,10 @@ from tests.parity import alm_err, zeta_err
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
+# Pair sums sum_p w_p sum_{j in b} w_j with positive weights: FP32 sums of at
+# most a few thousand weights per (primary, bin) (relative error well under
+# 1e-6 at random rounding), then FP64 over the primaries.
+PAIRSUM_RTOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -53,6 +57,8 @@ def test_small_thomas_vs_oracle(ctbmod, box, lmax):
     ref = oracle.zeta(xyz, w, **kw)
     assert est.pair_count() == ref["npairs"]
     assert zeta_err(z, ref) < TOL_FP32
+    # the two-point pair sums of the same pass (a_00 column)
+    np.testing.assert_allclose(est.pair_sums(), ref["wpairs"], rtol=PAIRSUM_RTOL)
 
 
 def test_uniform_20k_full_vs_oracle(ctbmod):
@@ -86,15 +92,55 @@ def test_alm_vs_oracle(ctbmod):
     assert alm_err(a, a_ref, w2, 10) < TOL_FP32
 
 
-@pytest.mark.parametrize("cap", [256, 4096])
+@pytest.mark.parametrize("cap", [0, 4096])
 @pytest.mark.parametrize("cpr", [1, 3, 16])
 def test_grid_and_list_capacity_do_not_change_result(ctbmod, cap, cpr):
-    """Cell size and per-bin list capacity (overflow -> several runs per bin)."""
+    """Cell size and list capacity (4096 entries: hundreds of chunks of a few
+    primaries, so chunk sizing, halving and bin-code buffer regrowth all run)."""
     xyz, w = synth.thomas(6000, 200.0, 30, 4.0, seed=25, weights="u0.5-1.5")
     kw = dict(box=200.0, rmin=1.0, rmax=40.0, nbins=4, lmax=4)
-    z, _ = run_full(ctbmod, xyz, w, kw, bin_capacity=cap, cells_per_rmax=cpr)
+    z, est = run_full(ctbmod, xyz, w, kw, list_capacity=cap, cells_per_rmax=cpr)
     ref = oracle.zeta(xyz, w, **kw)
+    assert est.pair_count() == ref["npairs"]
     assert zeta_err(z, ref) < TOL_FP32
+    if cap:
+        assert est.chunk_count() > 100
+
+
+def test_autotune_picks_a_grid_and_keeps_the_result(ctbmod):
+    xyz, w = synth.thomas(20000, 400.0, 100, 5.0, seed=31, weights="u0.5-1.5")
+    kw = dict(box=400.0, rmin=2.0, rmax=60.0, nbins=8, lmax=6)
+    plain = make(ctbmod, **kw)
+    plain.set_points(xyz, w)
+    assert plain.grid() == (8, int(np.floor(400.0 * 8 / 60.0)))
+    est = make(ctbmod, **kw, autotune=1)
+    est.set_points(xyz, w)
+    k, nc = est.grid()
+    assert k in (3, 4, 6, 8, 12, 16)
+    assert nc == min(1024, int(np.floor(400.0 * k / 60.0)))
+    z = est.compute()
+    ref = oracle.zeta(xyz, w, **kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < TOL_FP32
+    # the choice stays with the context for its next catalogue
+    est.set_points(xyz[:10000], w[:10000])
+    assert est.grid()[0] == k
+    # an explicit cell size wins over the tuner
+    fixed = make(ctbmod, **kw, autotune=1, cells_per_rmax=3)
+    fixed.set_points(xyz, w)
+    assert fixed.grid()[0] == 3
+
+
+def test_list_capacity_below_one_primary_is_oom(ctbmod):
+    xyz, w = synth.uniform(3000, 100.0, seed=26)
+    est = make(ctbmod, box=100.0, rmin=1.0, rmax=45.0, nbins=3, lmax=2, list_capacity=4096)
+    est.set_points(xyz, w)  # about 1130 neighbours per primary: fits
+    est.compute()
+    dense = np.concatenate([xyz, np.full((5000, 3), 50.0) + np.random.default_rng(3).uniform(-3, 3, (5000, 3))])
+    est.set_points(dense, None)  # 5000 more points in a 6-unit cube: each of them has > 4096 pairs
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.compute()
+    assert e.value.code == ctbmod.ERR_OOM
 
 
 def test_subset_and_partition(ctbmod):
@@ -105,12 +151,22 @@ def test_subset_and_partition(ctbmod):
     zfull = est.compute()
     perm = np.random.default_rng(0).permutation(xyz.shape[0])
     parts = [perm[:1000], perm[1000:3500], perm[3500:]]
-    zs = [est.compute_subset(p) for p in parts]
+    zs, ps = [], []
+    for p in parts:
+        zs.append(est.compute_subset(p))
+        ps.append(est.pair_sums())
     ref = oracle.zeta(xyz, w, prim=parts[0], **kw)
     assert zeta_err(zs[0], ref) < TOL_FP32
+    np.testing.assert_allclose(ps[0], ref["wpairs"], rtol=PAIRSUM_RTOL)
     reff = oracle.zeta(xyz, w, **kw)
     assert zeta_err(sum(zs), reff) < TOL_FP32
     assert zeta_err(zfull, reff) < TOL_FP32
+    np.testing.assert_allclose(sum(ps), reff["wpairs"], rtol=PAIRSUM_RTOL)
+    # a new catalogue has no pair sums until its first compute
+    est.set_points(xyz[:100], w[:100])
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.pair_sums()
+    assert e.value.code == ctbmod.ERR_STATE
 
 
 # ------------------------------------------------------------------ edge cases
@@ -310,15 +366,19 @@ def test_batch_matches_single_catalogues(ctbmod, prec):
     zb = est.compute_batch(cats)
     assert zb.shape == (len(sizes), 9, 6, 6)
     assert np.all(zb[1] == 0)
+    pb = est.pair_sums(len(sizes))
+    assert np.all(pb[1] == 0)
     tol = TOL_FP32 if prec == "FP32" else TOL_MIXED
     for i, (xyz, w) in enumerate(cats):
         if sizes[i] == 0:
             continue
-        zs, _ = run_full(ctbmod, xyz, w, kw, **opts)
+        zs, single = run_full(ctbmod, xyz, w, kw, **opts)
+        np.testing.assert_allclose(pb[i], single.pair_sums(), rtol=PAIRSUM_RTOL)
         ref = oracle.zeta(xyz, w, **kw) if i in (2, 3) else None
         if ref is not None:
             assert zeta_err(zb[i], ref) < tol
             assert zeta_err(zs, ref) < tol
+            np.testing.assert_allclose(pb[i], ref["wpairs"], rtol=PAIRSUM_RTOL)
         scale = np.abs(zs).max()
         assert np.max(np.abs(zb[i] - zs)) <= 1e-6 * scale
     # the batch replaced the context's catalogue
