@@ -44,7 +44,7 @@ INST_PER_UPDATE = 2.6
 # DRAM bytes per pair of the accumulation kernel from one ncu capture of the
 # current k_alm (dram__bytes_read.sum + dram__bytes_write.sum over the pairs of
 # the captured launch); None when the kernel changed after the capture.
-K_ALM_DRAM_BYTES_PER_PAIR = None
+K_ALM_DRAM_BYTES_PER_PAIR = 4.347
 FP32_LANES_PER_SM = 128
 
 
@@ -74,6 +74,14 @@ def workload(name: str):
             "workload": "thomas_4m", "n_points": 4_000_000, "box": 2000.0, "r_min": 10.0, "r_max": 200.0,
             "nbins": 32, "ell_max": 20, "periodic": True, "clustering": "Thomas, 40k parents, sigma 5",
             "weights": "U[0.5,1.5]"}
+    if name == "mock_batch":
+        sizes = synth.mock_sizes()
+        cats = [synth.mock_catalogue(i, n) for i, n in enumerate(sizes)]
+        return [c[0] for c in cats], [np.ones(c[0].shape[0]) for c in cats], synth.config_params(4), {
+            "workload": "mock_batch", "catalogues": len(sizes), "n_points": int(sizes.sum()), "box": 1000.0,
+            "r_min": 10.0, "r_max": 150.0, "nbins": 20, "ell_max": 10, "periodic": True,
+            "clustering": "Thomas per catalogue, N_i/100 parents, sigma 5", "weights": "unit",
+            "mode": "one ctb_compute_batch call per step"}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -126,6 +134,23 @@ def traffic_per_launch(npairs: int, chunks: int):
     if K_ALM_DRAM_BYTES_PER_PAIR is None or chunks <= 0:
         return None
     return K_ALM_DRAM_BYTES_PER_PAIR * npairs / chunks
+
+
+def contraction_roofline(args, kw, stages_ms, cfg, pk, pk_kind, npts):
+    """Tensor-pipe roofline of the tcgen05 contraction (mixed precisions only):
+    2 * primaries * (l_max+1)^2 * nbins^2 FLOPs per step (x3 for the BF16 hi/lo
+    split) over the contraction stage's event time, against the measured dense
+    BF16 peak (TF32: x 1.1/2.25, the nominal TF32/BF16 ratio)."""
+    if args.precision == "fp32" or stages_ms.get("contraction", 0.0) <= 0.0:
+        return {}
+    nc = (kw["lmax"] + 1) ** 2
+    flops = 2.0 * npts * nc * kw["nbins"] ** 2 * (3 if args.precision == "bf16x3" else 1)
+    peak = float(pk.get("bf16_tflops", 1900.0)) * (1.0 if args.precision == "bf16x3" else 1.1 / 2.25)
+    achieved = flops / (stages_ms["contraction"] / 1e3) / 1e12
+    return {"roofline_contraction": {"bound": "tensor", "kernel": "k_contract_tc", "achieved": achieved,
+                                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                     "peak_note": f"dense BF16 ({pk_kind}, burst)"
+                                                  + (" x 1.1/2.25 for TF32" if args.precision == "tf32" else "")}}
 
 
 def peaks():
@@ -227,7 +252,16 @@ def max_over_ranks(world, v: float) -> float:
 # CPU oracle timing (reference arm and cpu_baseline)
 
 
-def oracle_rate(xyz, w, kw, target_s: float, seed: int = 7):
+def zeta_err(z, ref) -> float:
+    """max over (l, b1, b2) of |z - zeta_ref| / sqrt(G_l(b1,b1) G_l(b2,b2)), G the
+    same contraction with |w_p| (a Cauchy-Schwarz bound on every entry)."""
+    g = np.abs(np.diagonal(ref["gram"], axis1=1, axis2=2))
+    s = np.sqrt(g[:, :, None] * g[:, None, :])
+    d = np.abs(np.asarray(z) - ref["zeta"])
+    return float(np.max(np.where(s > 0, d / np.where(s > 0, s, 1.0), np.where(d > 0, np.inf, 0.0))))
+
+
+def oracle_rate(xyz, w, kw, target_s: float, seed: int = 7, full: bool = False):
     """Time the oracle on a growing sample of primaries until ~target_s of CPU work."""
     import oracle
     from paper_2604_08855_gb300 import synth
@@ -242,6 +276,8 @@ def oracle_rate(xyz, w, kw, target_s: float, seed: int = 7):
         if dt >= 0.25 * target_s or k >= xyz.shape[0]:
             break
         k = min(xyz.shape[0], int(k * max(2.0, min(16.0, 0.5 * target_s / max(dt, 1e-3)))))
+    if full:
+        return res["npairs"] * nc / dt, k, dt, res["npairs"], res
     return res["npairs"] * nc / dt, k, dt, res["npairs"]
 
 
@@ -250,14 +286,17 @@ def run_reference(args):
     if rank != 0:
         return
     xyz, w, kw, cfg = workload(args.workload)
+    if isinstance(xyz, list):  # a batch: the oracle samples catalogue 0
+        xyz, w = xyz[0], w[0]
+        cfg = {**cfg, "note": "oracle sample from catalogue 0"}
     import oracle
     oracle.build()
     from paper_2604_08855_gb300 import synth
     nc = (kw["lmax"] + 1) ** 2
     cores = oracle.max_threads()
     # size the per-step sample to about 2 s of CPU work
-    rate, _, _, _ = oracle_rate(xyz, w, kw, target_s=2.0)
-    per_pair = max(1.0, 33510.0 if args.workload == "thomas_1m" else 84.0)
+    rate, k0, _, np0 = oracle_rate(xyz, w, kw, target_s=2.0)
+    per_pair = max(1.0, np0 / max(k0, 1))  # pairs per primary of the sample
     k = int(max(8, min(xyz.shape[0], 2.0 * rate / nc / per_pair)))
     times, pairs = [], []
     for step in range(args.warmup + args.steps):
@@ -303,22 +342,30 @@ def run_ours(args):
     est.set_stream(stream)
     if args.precision != "fp32":
         est.set_option(ctb.OPT_PRECISION, {"bf16x3": ctb.PREC_BF16X3, "tf32": ctb.PREC_TF32}[args.precision])
+    batch = isinstance(xyz, list)  # several catalogues, one ctb_compute_batch per step
     if args.cells_per_rmax:
         est.set_option(ctb.OPT_CELLS_PER_RMAX, args.cells_per_rmax)
-    else:
+    elif not batch:
         est.set_option(ctb.OPT_AUTOTUNE, 1)  # tuned on the first set_points (a warm-up step)
-    d_xyz = torch.from_numpy(xyz).to(dev)
-    d_w = torch.from_numpy(w).to(dev)
-    d_zeta = torch.zeros(est.zeta_shape, dtype=torch.float64, device=dev)
+    if batch:
+        d_cats = [(torch.from_numpy(x).to(dev), torch.from_numpy(v).to(dev)) for x, v in zip(xyz, w)]
+        d_zeta = torch.zeros((len(xyz),) + est.zeta_shape, dtype=torch.float64, device=dev)
+    else:
+        d_xyz = torch.from_numpy(xyz).to(dev)
+        d_w = torch.from_numpy(w).to(dev)
+        d_zeta = torch.zeros(est.zeta_shape, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     d_prim = None
-    if args.primaries:
+    if args.primaries and not batch:
         # profiling case: the same catalogue and kernels, fewer primaries
         from paper_2604_08855_gb300 import synth
         d_prim = torch.from_numpy(synth.sample_primaries(xyz.shape[0], args.primaries, seed=7)).to(dev)
         cfg = {**cfg, "primaries": args.primaries, "note": "primary subset (profiling case)"}
 
     def step():
+        if batch:
+            est.compute_batch(d_cats, out=d_zeta)
+            return
         est.set_points(d_xyz, d_w)
         if d_prim is None:
             est.compute(out=d_zeta)
@@ -357,20 +404,26 @@ def run_ours(args):
     ms_per_step = 1e3 * t_total / args.steps
 
     # end to end through the public API with host buffers
-    zh = np.zeros(est.zeta_shape)
+    zh = np.zeros(tuple(d_zeta.shape))
     e2e_t = []
     for k in range(0 if args.no_e2e else max(2, min(args.steps, 5)) + 1):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        est.set_points(xyz, w)
-        est.compute(out=zh)
+        if batch:
+            est.compute_batch(list(zip(xyz, w)), out=zh)
+        else:
+            est.set_points(xyz, w)
+            est.compute(out=zh)
         dt = time.perf_counter() - t0
         if k > 0:
             e2e_t.append(dt)
     e2e_s = max_over_ranks(world, float(np.mean(e2e_t)) if e2e_t else float("nan"))
+    in_bytes = sum(a.nbytes for a in xyz) + sum(a.nbytes for a in w) if batch else xyz.nbytes + w.nbytes
     e2e = {"value": world * updates / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(xyz.nbytes + w.nbytes), "d2h_bytes_per_step": int(zh.nbytes + 8)}
+           "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(zh.nbytes + 8)}
 
+    n_prim_step = (sum(a.shape[0] for a in xyz) if batch else xyz.shape[0]) if not args.primaries \
+        else args.primaries
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     # FP32 lane-instruction peak (one FMA-pipe instruction per lane per clock)
@@ -388,8 +441,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**cfg, "precision": args.precision, "cells_per_rmax": est.grid()[0],
-                   "grid": "fixed" if args.cells_per_rmax else "autotuned",
+        "config": {**cfg, "precision": args.precision,
+                   "cells_per_rmax": args.cells_per_rmax or 8 if batch else est.grid()[0],
+                   "grid": "fixed" if args.cells_per_rmax or batch else "autotuned",
                    "l2": "flushed (256 MB write) before every step",
                    "inputs": "device-resident float64 xyz, w"},
         "e2e": e2e,
@@ -403,6 +457,7 @@ def run_ours(args):
                      "impl_flops_per_pair": flops_per_pair(kw["lmax"]), "impl_tflops": impl_tflops,
                      "impl_frac": impl_tflops / (2 * peak_tinst), "kernel_ms": 1e3 * pair_s},
         "stages_ms": stages_ms,
+        **contraction_roofline(args, kw, stages_ms, cfg, pk, pk_kind, npts=n_prim_step),
         "pairs_per_step": npairs,
         "pairs_per_s": world * args.steps * npairs / t_total,
         "ms_per_zeta_ell": ms_per_step / (kw["lmax"] + 1),
@@ -410,10 +465,20 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        rate, k, dt, _ = oracle_rate(xyz, w, kw, target_s=args.cpu_seconds)
+        sx, sw = (xyz[0], w[0]) if batch else (xyz, w)
+        rate, k, dt, _, ref = oracle_rate(sx, sw, kw, target_s=args.cpu_seconds, full=True)
         import oracle
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                                "sample": f"{k} seeded primaries x all {xyz.shape[0]} secondaries, {dt:.1f} s"}
+                                "sample": f"{k} seeded primaries x all {sx.shape[0]} secondaries"
+                                          + (" of catalogue 0" if batch else "") + f", {dt:.1f} s"}
+        # the same primaries through the library, against the oracle
+        from paper_2604_08855_gb300 import synth
+        prim = synth.sample_primaries(sx.shape[0], k, seed=7)
+        est.set_points(sx, sw)
+        z = est.compute_subset(prim)
+        line["parity"] = {"metric": "max |dzeta| / sqrt(G(b1,b1) G(b2,b2)), G the |w_p| Gram",
+                          "value": zeta_err(z, ref), "tolerance": 1e-5 if args.precision == "fp32" else 1e-3,
+                          "sample": f"the cpu_baseline's {k} primaries", "pairs_match": est.pair_count() == ref["npairs"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     est.close()
