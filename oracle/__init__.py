@@ -13,9 +13,13 @@ Parity status of each function (what pins it is listed in the tests):
   zeta   pinned: O(N^3) triplet sum with numpy Legendre polynomials, the
          l = 0 closed form with scipy's cKDTree neighbour counts, hand-built
          geometries with printed P_l values, invariances.
+  zeta_sphere  pinned: frame-free triplet sum (angles between tangent
+         projections), the m = 0 closed form with scipy's cKDTree chord
+         counts, a hand geometry at the pole and on the equator, rotation
+         invariance.
   edge.edge_correct  pinned: sympy's Wigner 3j symbols, exact Legendre
          quotients built with numpy's legmul, flat randoms (plain ratio),
          quadrature of N/R.
 """
-from .oracle import build, ylm, alm, zeta, max_threads, lib_path  # noqa: F401
+from .oracle import build, ylm, alm, zeta, zeta_sphere, max_threads, lib_path  # noqa: F401
 from . import edge  # noqa: F401

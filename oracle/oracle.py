@@ -14,6 +14,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ctb_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "ctb_oracle_sphere.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libctb_oracle.so")
 _lock = threading.Lock()
@@ -27,11 +28,11 @@ def lib_path() -> str:
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP, IEEE arithmetic)."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS):
             os.makedirs(_BUILD, exist_ok=True)
             tmp = _LIB + f".tmp{os.getpid()}"
             cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-                   "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+                   "-fno-fast-math", "-ffp-contract=off", "-o", tmp, *_SRCS, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB)
     return _LIB
@@ -51,6 +52,8 @@ def _load():
         lib.oracle_zeta.argtypes = [vp, vp, i64, d, d, d, i32, i32, vp, i64,
                                     vp, vp, vp, vp, vp, vp, d, i32]
         lib.oracle_zeta.restype = i32
+        lib.oracle_zeta_sphere.argtypes = [vp, vp, i64, d, d, i32, i32, vp, i64, vp, vp, vp, vp, i32]
+        lib.oracle_zeta_sphere.restype = i32
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = i32
         _lib = lib
@@ -139,3 +142,28 @@ def zeta(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, amb_tol=0.0, nthreads=
         raise ValueError(f"oracle_zeta rejected its arguments (rc={rc})")
     return {"zeta": z, "gram": g, "wpairs": wp, "selfw": sw,
             "npairs": int(npairs.value), "namb": int(namb.value)}
+
+
+def zeta_sphere(xyz, w, theta_min, theta_max, nbins, mmax, prim=None, nthreads=0):
+    """Projected (angular) multipoles zeta_m(b1, b2) on the unit sphere, summed
+    over the given primaries (ctb_oracle_sphere.c states the definition).
+
+    Returns a dict with ``zeta`` and ``gram`` ([mmax+1][nbins][nbins]),
+    ``wpairs`` ([nbins]) and ``npairs``.
+    """
+    lib = _load()
+    xyz, w = _points(xyz, w)
+    prim = _prim(prim)
+    n = xyz.shape[0]
+    np_ = n if prim is None else prim.shape[0]
+    shape = (mmax + 1, nbins, nbins)
+    z = np.zeros(shape)
+    g = np.zeros(shape)
+    wp = np.zeros(nbins)
+    npairs = ctypes.c_int64(0)
+    rc = lib.oracle_zeta_sphere(_ptr(xyz), _ptr(w), n, float(theta_min), float(theta_max), int(nbins),
+                                int(mmax), _ptr(prim), np_, _ptr(z), _ptr(g), _ptr(wp),
+                                ctypes.byref(npairs), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_zeta_sphere rejected its arguments (rc={rc})")
+    return {"zeta": z, "gram": g, "wpairs": wp, "npairs": int(npairs.value)}
