@@ -74,6 +74,14 @@ def workload(name: str):
             "workload": "thomas_4m", "n_points": 4_000_000, "box": 2000.0, "r_min": 10.0, "r_max": 200.0,
             "nbins": 32, "ell_max": 20, "periodic": True, "clustering": "Thomas, 40k parents, sigma 5",
             "weights": "U[0.5,1.5]"}
+    if name == "sphere_nside1024":
+        xyz, w = synth.sphere_map(1024)
+        arcmin = np.pi / (180.0 * 60.0)
+        return xyz, w, dict(sphere=True, theta_min=0.0, theta_max=200.0 * arcmin, nbins=20, mmax=8), {
+            "workload": "sphere_nside1024", "n_points": int(xyz.shape[0]), "geometry": "unit sphere",
+            "theta_arcmin": [0.0, 200.0], "nbins": 20, "m_max": 8,
+            "points": "12 * 1024^2 Fibonacci-spiral directions (equal-area, HEALPix-like)",
+            "weights": "smooth random field: 64 von Mises blobs (width 0.05 rad) + 0.1 white noise"}
     if name == "mock_batch":
         sizes = synth.mock_sizes()
         cats = [synth.mock_catalogue(i, n) for i, n in enumerate(sizes)]
@@ -81,7 +89,7 @@ def workload(name: str):
             "workload": "mock_batch", "catalogues": len(sizes), "n_points": int(sizes.sum()), "box": 1000.0,
             "r_min": 10.0, "r_max": 150.0, "nbins": 20, "ell_max": 10, "periodic": True,
             "clustering": "Thomas per catalogue, N_i/100 parents, sigma 5", "weights": "unit",
-            "mode": "one ctb_compute_batch call per step"}
+            "mode": "see batch_mode"}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -143,7 +151,7 @@ def contraction_roofline(args, kw, stages_ms, cfg, pk, pk_kind, npts):
     BF16 peak (TF32: x 1.1/2.25, the nominal TF32/BF16 ratio)."""
     if args.precision == "fp32" or stages_ms.get("contraction", 0.0) <= 0.0:
         return {}
-    nc = (kw["lmax"] + 1) ** 2
+    nc = ncoef(kw)
     flops = 2.0 * npts * nc * kw["nbins"] ** 2 * (3 if args.precision == "bf16x3" else 1)
     peak = float(pk.get("bf16_tflops", 1900.0)) * (1.0 if args.precision == "bf16x3" else 1.1 / 2.25)
     achieved = flops / (stages_ms["contraction"] / 1e3) / 1e12
@@ -252,6 +260,24 @@ def max_over_ranks(world, v: float) -> float:
 # CPU oracle timing (reference arm and cpu_baseline)
 
 
+def ncoef(kw) -> int:
+    """Real coefficients per pair: (l_max+1)^2 in 3-D, 2 m_max + 1 on the sphere."""
+    return 2 * kw["mmax"] + 1 if kw.get("sphere") else (kw["lmax"] + 1) ** 2
+
+
+def oracle_zeta(xyz, w, kw, prim):
+    import oracle
+    if kw.get("sphere"):
+        return oracle.zeta_sphere(xyz, w, kw["theta_min"], kw["theta_max"], kw["nbins"], kw["mmax"], prim=prim)
+    return oracle.zeta(xyz, w, prim=prim, **kw)
+
+
+def make_estimator(ctb, kw):
+    if kw.get("sphere"):
+        return ctb.CTB.sphere(kw["theta_min"], kw["theta_max"], kw["nbins"], kw["mmax"])
+    return ctb.CTB(**kw)
+
+
 def zeta_err(z, ref) -> float:
     """max over (l, b1, b2) of |z - zeta_ref| / sqrt(G_l(b1,b1) G_l(b2,b2)), G the
     same contraction with |w_p| (a Cauchy-Schwarz bound on every entry)."""
@@ -266,12 +292,12 @@ def oracle_rate(xyz, w, kw, target_s: float, seed: int = 7, full: bool = False):
     import oracle
     from paper_2604_08855_gb300 import synth
     oracle.build()
-    nc = (kw["lmax"] + 1) ** 2
+    nc = ncoef(kw)
     k = 32
     while True:
         prim = synth.sample_primaries(xyz.shape[0], k, seed=seed)
         t0 = time.perf_counter()
-        res = oracle.zeta(xyz, w, prim=prim, **kw)
+        res = oracle_zeta(xyz, w, kw, prim)
         dt = time.perf_counter() - t0
         if dt >= 0.25 * target_s or k >= xyz.shape[0]:
             break
@@ -292,7 +318,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     from paper_2604_08855_gb300 import synth
-    nc = (kw["lmax"] + 1) ** 2
+    nc = ncoef(kw)
     cores = oracle.max_threads()
     # size the per-step sample to about 2 s of CPU work
     rate, k0, _, np0 = oracle_rate(xyz, w, kw, target_s=2.0)
@@ -302,7 +328,7 @@ def run_reference(args):
     for step in range(args.warmup + args.steps):
         prim = synth.sample_primaries(xyz.shape[0], k, seed=1000 + step)
         t0 = time.perf_counter()
-        res = oracle.zeta(xyz, w, prim=prim, **kw)
+        res = oracle_zeta(xyz, w, kw, prim)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
@@ -336,8 +362,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     xyz, w, kw, cfg = workload(args.workload)
-    nc = (kw["lmax"] + 1) ** 2
-    est = ctb.CTB(**kw)
+    nc = ncoef(kw)
+    est = make_estimator(ctb, kw)
     stream = torch.cuda.current_stream(dev)
     est.set_stream(stream)
     if args.precision != "fp32":
@@ -362,7 +388,22 @@ def run_ours(args):
         d_prim = torch.from_numpy(synth.sample_primaries(xyz.shape[0], args.primaries, seed=7)).to(dev)
         cfg = {**cfg, "primaries": args.primaries, "note": "primary subset (profiling case)"}
 
+    seq = batch and args.batch_mode == "sequential"
+    seq_stats = {}
+
     def step():
+        if seq:
+            # the same catalogues as plain launches, one set_points + compute each
+            tm, launches_, pairs_, chunks_ = np.zeros(8), 0, 0, 0
+            for i, (x, v) in enumerate(d_cats):
+                est.set_points(x, v)
+                est.compute(out=d_zeta[i])
+                tm += np.array(est.timings())
+                launches_ += est.launch_count()
+                pairs_ += est.pair_count()
+                chunks_ += est.chunk_count()
+            seq_stats.update(timings=list(tm), launches=launches_, pairs=pairs_, chunks=chunks_)
+            return
         if batch:
             est.compute_batch(d_cats, out=d_zeta)
             return
@@ -388,12 +429,17 @@ def run_ours(args):
             ev[k][0].record(stream)
             step()
             ev[k][1].record(stream)
-            tm = est.timings()
+            if seq:
+                tm = seq_stats["timings"]
+                launches += seq_stats["launches"]
+                npairs, chunks = seq_stats["pairs"], seq_stats["chunks"]
+            else:
+                tm = est.timings()
+                launches += est.launch_count()
+                npairs = est.pair_count()
+                chunks = est.chunk_count()
             pair_ms.append(tm[7])
             stages.append(tm)
-            launches += est.launch_count()
-            npairs = est.pair_count()
-            chunks = est.chunk_count()
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - wall0
     barrier(world)
@@ -409,7 +455,11 @@ def run_ours(args):
     for k in range(0 if args.no_e2e else max(2, min(args.steps, 5)) + 1):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        if batch:
+        if seq:
+            for i, (x, v) in enumerate(zip(xyz, w)):
+                est.set_points(x, v)
+                est.compute(out=zh[i])
+        elif batch:
             est.compute_batch(list(zip(xyz, w)), out=zh)
         else:
             est.set_points(xyz, w)
@@ -429,10 +479,23 @@ def run_ours(args):
     # FP32 lane-instruction peak (one FMA-pipe instruction per lane per clock)
     peak_tinst = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     pair_s = float(np.mean(pair_ms)) / 1e3
-    # algorithmic work of the accumulation: INST_PER_UPDATE FP32 instructions
-    # per (pair, coefficient) update, over the kernel's own event time
-    achieved = npairs * nc * INST_PER_UPDATE / pair_s / 1e12
-    impl_tflops = npairs * flops_per_pair(kw["lmax"]) / pair_s / 1e12
+    sphere = bool(kw.get("sphere"))
+    n_groups = (kw["mmax"] if sphere else kw["lmax"]) + 1
+    if sphere:
+        # per pair: the Chebyshev recurrence (2 per m: cos and sin), one
+        # accumulate per real coefficient, ~10 for the tangent projection
+        inst_pair = 4 * kw["mmax"] + 11
+        achieved = npairs * inst_pair / pair_s / 1e12
+        roof = {"kernel": "k_am", "work_per_unit": f"{inst_pair} FP32 instructions per pair (4 m_max + 11)"}
+    else:
+        # algorithmic work of the accumulation: INST_PER_UPDATE FP32 instructions
+        # per (pair, coefficient) update, over the kernel's own event time
+        achieved = npairs * nc * INST_PER_UPDATE / pair_s / 1e12
+        impl_tflops = npairs * flops_per_pair(kw["lmax"]) / pair_s / 1e12
+        roof = {"kernel": "k_alm", "work_per_unit": f"{INST_PER_UPDATE} FP32 instructions per update",
+                "traffic": traffic_per_launch(npairs, chunks),
+                "impl_flops_per_pair": flops_per_pair(kw["lmax"]), "impl_tflops": impl_tflops,
+                "impl_frac": impl_tflops / (2 * peak_tinst)}
     st = np.mean(np.array(stages), axis=0)
     names = ["ingest", "sort_grid", "pair_total", "pack", "contraction", "reduce", "enumerate", "accumulate"]
     stages_ms = {k: round(float(v), 3) for k, v in zip(names, st)}
@@ -441,26 +504,23 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**cfg, "precision": args.precision,
+        "config": {**cfg, "precision": args.precision, **({"batch_mode": args.batch_mode} if batch else {}),
                    "cells_per_rmax": args.cells_per_rmax or 8 if batch else est.grid()[0],
                    "grid": "fixed" if args.cells_per_rmax or batch else "autotuned",
                    "l2": "flushed (256 MB write) before every step",
                    "inputs": "device-resident float64 xyz, w"},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_alm", "achieved": achieved, "peak": peak_tinst,
-                     "unit": "Tinst/s", "frac": achieved / peak_tinst, "traffic": traffic_per_launch(npairs, chunks),
-                     "launches_per_step": chunks,
-                     "work_per_unit": f"{INST_PER_UPDATE} FP32 instructions per update",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+                     "frac": achieved / peak_tinst, "traffic": None, **roof, "launches_per_step": chunks,
                      "peak_note": f"FP32 pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
                                   f"{sm_max:.0f} MHz ({pk_kind} max clock)",
-                     "impl_flops_per_pair": flops_per_pair(kw["lmax"]), "impl_tflops": impl_tflops,
-                     "impl_frac": impl_tflops / (2 * peak_tinst), "kernel_ms": 1e3 * pair_s},
+                     "kernel_ms": 1e3 * pair_s},
         "stages_ms": stages_ms,
         **contraction_roofline(args, kw, stages_ms, cfg, pk, pk_kind, npts=n_prim_step),
         "pairs_per_step": npairs,
         "pairs_per_s": world * args.steps * npairs / t_total,
-        "ms_per_zeta_ell": ms_per_step / (kw["lmax"] + 1),
+        "ms_per_zeta_ell": ms_per_step / n_groups,
         "wall_s": wall,
         "clocks": clocks,
     }
@@ -497,6 +557,8 @@ def main():
     ap.add_argument("--primaries", type=int, default=0,
                     help="profiling case: time ctb_compute_subset over this many seeded primaries")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-mode", default="batched", choices=["batched", "sequential"],
+                    help="mock_batch: one ctb_compute_batch per step, or one set_points + compute per catalogue")
     ap.add_argument("--cells-per-rmax", type=int, default=0,
                     help="grid cells per r_max (0: the library's autotuner picks)")
     args = ap.parse_args()

@@ -61,6 +61,8 @@ typedef struct ctb_ctx ctb_ctx;
 #define CTB_LMAX_CAP 20
 /* largest number of radial bins a context accepts */
 #define CTB_NBINS_CAP 64
+/* largest m_max of a sphere context (ctb_create_sphere) */
+#define CTB_MMAX_CAP 16
 
 /* option keys for ctb_set_option */
 #define CTB_OPT_PRECISION 1      /* contraction precision, CTB_PREC_* (default FP32)        */
@@ -98,6 +100,31 @@ typedef struct ctb_ctx ctb_ctx;
  * CUDA device current at this call.
  */
 ctb_ctx* ctb_create(double box, double r_min, double r_max, int nbins, int ell_max);
+
+/*
+ * Projected (angular) multipoles of a scalar field on the unit sphere -- the
+ * paper's own workload ("Statement of need": 3PCF multipoles for projected
+ * fields such as the weak-lensing convergence; "Implementation": a harmonic
+ * decomposition of one angle of the triangle, sin and cos by a Chebyshev
+ * recurrence).  Points passed to ctb_set_points are directions (unit
+ * vectors, float64 xyz, not re-normalised), weights the field values.
+ *   separation  theta = 2 asin(|n_j - n_p| / 2), bins linear in theta on
+ *               [theta_min, theta_max) (radians; theta_max <= pi), decided
+ *               exactly on the chord against 2 sin(theta_b / 2) in FP64
+ *   angle       phi_pj = atan2(u, v): u, v the components of n_j - n_p on the
+ *               east and north unit vectors of p's tangent plane (at a pole
+ *               east = +y); phi = 0 when both vanish
+ *   a_m(p,b)    = sum_{j != p in b} w_j exp(i m phi_pj), m = 0..m_max
+ *   zeta_m(b1,b2) = sum_p w_p Re[a_m(p,b1) conj(a_m(p,b2))]   (no 4 pi factor)
+ * ctb_compute writes zeta_m as [(m_max+1)][nbins][nbins]; ctb_get_alm writes
+ * [primary][bin][2 m_max + 1] as (a_0, Re a_1, Im a_1, ..., Re a_mmax, Im a_mmax)
+ * in the library's tangent frame; ctb_get_2pcf gives sum_p w_p sum_{j in b} w_j.
+ * zeta_m does not depend on the tangent frame.  The contraction runs in FP32
+ * (CTB_OPT_PRECISION other than FP32, ctb_compute_batch and ctb_edge_correct
+ * return CTB_ERR_UNSUPPORTED).  m_max in [0, CTB_MMAX_CAP]; NULL on bad
+ * arguments (message from ctb_last_error(NULL)).
+ */
+ctb_ctx* ctb_create_sphere(double theta_min, double theta_max, int nbins, int m_max);
 
 /*
  * Load a catalogue (paper, "Implementation": the points that act as pivots

@@ -36,6 +36,8 @@ struct ctb_ctx {
   // options
   int precision = CTB_PREC_FP32;
   int cells_per_rmax = 0;
+  int sphere = 0;            // projected multipoles on the unit sphere (lmax holds m_max)
+  double tmin = 0, tmax = 0;  // sphere: angular bin range (radians)
   int autotune = 0;
   int inject = 0;     // CTB_INJECT_* test hook
   int tuned_cpr = 0;  // cells per r_max chosen by the autotuner (0: none yet)
@@ -170,8 +172,35 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 }
 
 // normalisation per slot and the slot table of the context's layout
+int ensure_tables_sphere(ctb_ctx* c) {
+  // row = [a_0, Re a_1, Im a_1, ...], padded to 32; every slot its own coefficient
+  const int nc = 2 * c->lmax + 1;
+  Layout& y = c->lay;
+  y = Layout{};
+  y.L = c->lmax;
+  y.npass = 1;
+  y.row = ((nc + 31) / 32) * 32;
+  for (int i = 0; i < (kLmaxCap + 1) * (kLmaxCap + 1); ++i) y.slot[i] = i < nc ? i : -1;
+  std::vector<int> coff(y.row + 1), csrc(y.row);
+  std::vector<float> ccoef(y.row, 1.f);
+  for (int k = 0; k <= y.row; ++k) coff[k] = k;
+  for (int k = 0; k < y.row; ++k) csrc[k] = k;
+  CK(c, ensure(c, c->slot, sizeof(y.slot)));
+  CK(c, cudaMemcpyAsync(c->slot.p, y.slot, sizeof(y.slot), cudaMemcpyHostToDevice, c->st));
+  CK(c, ensure(c, c->conv_off, coff.size() * sizeof(int)));
+  CK(c, ensure(c, c->conv_src, csrc.size() * sizeof(int)));
+  CK(c, ensure(c, c->conv_coef, ccoef.size() * sizeof(float)));
+  CK(c, cudaMemcpyAsync(c->conv_off.p, coff.data(), coff.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->conv_src.p, csrc.data(), csrc.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->conv_coef.p, ccoef.data(), ccoef.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaStreamSynchronize(c->st));  // host sources go out of scope
+  c->tables_ready = true;
+  return CTB_OK;
+}
+
 int ensure_tables(ctb_ctx* c) {
   if (c->tables_ready) return CTB_OK;
+  if (c->sphere) return ensure_tables_sphere(c);
   c->Lk = lmax_kernel(c->lmax);
   make_layout(c->Lk, &c->lay);
   fill_beta(c->beta);
@@ -291,6 +320,15 @@ namespace {
 // r_min, r_min + b (r_max - r_min)/nbins, r_max
 int upload_thresholds(ctb_ctx* c) {
   std::vector<unsigned long long> thr(c->nbins + 1);
+  if (c->sphere) {
+    // chord edges of the linear angular bins: 2 sin(theta_b / 2)
+    for (int b = 0; b <= c->nbins; ++b)
+      thr[b] = sq_threshold(2.0 * std::sin(0.5 * (c->tmin + b * (c->tmax - c->tmin) / c->nbins)), c->unit);
+    CK(c, ensure(c, c->thr, thr.size() * 8));
+    CK(c, cudaMemcpyAsync(c->thr.p, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    return CTB_OK;
+  }
   const double dr = (c->rmax - c->rmin) / c->nbins;
   thr[0] = sq_threshold(c->rmin, c->unit);
   for (int b = 1; b < c->nbins; ++b) {
@@ -315,6 +353,7 @@ void finish_geom(ctb_ctx* c, Geom& g, uint32_t nc) {
   g.inv_dr_u = (float)(c->nbins / (rmax_u - rmin_u));
   g.cell_scale = (float)(nc / std::ldexp(1.0, g.shift));
   g.rcell = (float)(rmax_u * nc / std::ldexp(1.0, g.shift) * (1.0 + 1e-5) + 1e-3);
+  g.general = c->sphere;
 }
 
 int bits_for(uint32_t ncells) {
@@ -482,9 +521,18 @@ struct PairPlan {
 // list entry of the list capacity.
 constexpr uint64_t kCodeCap = 1ull << 34;
 
+// Neighbours in range of a primary at the catalogue's mean density: the
+// ball's share of the box (3-D), or the ring's share of the sphere's area.
+double mean_neighbours(const ctb_ctx* c) {
+  if (c->sphere) return (double)c->n * 0.5 * (std::cos(c->tmin) - std::cos(c->tmax));
+  const double vol = c->periodic ? c->box * c->box * c->box : c->bbox_volume;
+  const double ball = 4.0 / 3.0 * M_PI * (c->rmax * c->rmax * c->rmax - c->rmin * c->rmin * c->rmin);
+  return vol > 0 ? (double)c->n * std::min(1.0, ball / vol) : 0.0;
+}
+
 int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   int wpb = c->wpb > 0 ? c->wpb : 4;
-  int bps = alm_blocks_per_sm(c->Lk, wpb);
+  int bps = c->sphere ? am_blocks_per_sm(c->lmax, wpb) : alm_blocks_per_sm(c->Lk, wpb);
   int sbps = stream_blocks_per_sm(true, c->nbins);
   int cbps = stream_blocks_per_sm(false, c->nbins);
   if (bps < 1 || sbps < 1 || cbps < 1) return fail(c, CTB_ERR_CUDA, "pair kernels cannot be resident");
@@ -499,7 +547,7 @@ int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   pl->nparts = 2 * c->nsm;
   if (c->precision == CTB_PREC_FP32) {
     // one wave of the FP32 contraction's resident blocks
-    const int cb = contract_fp32_blocks_per_sm(c->nbins, c->lmax, c->lay.row);
+    const int cb = contract_fp32_blocks_per_sm(c->nbins, c->lmax, c->lay.row, c->sphere);
     if (cb < 1) return fail(c, CTB_ERR_CUDA, "the contraction kernel cannot be resident");
     pl->ncon = cb * c->nsm;
   } else {
@@ -507,9 +555,7 @@ int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   }
   // first chunk from the mean density, with a margin for clustering; later
   // chunks follow the measured pairs per primary
-  const double vol = c->periodic ? c->box * c->box * c->box : c->bbox_volume;
-  const double ball = 4.0 / 3.0 * M_PI * (c->rmax * c->rmax * c->rmax - c->rmin * c->rmin * c->rmin);
-  const double est = vol > 0 ? 2.0 * (double)c->n * std::min(1.0, ball / vol) + 64.0 : 64.0;
+  const double est = 2.0 * mean_neighbours(c) + 64.0;
   // candidates (points of the scanned cell rows) run about 1.3-1.5x the pairs
   pl->code_cap = std::min<uint64_t>(kCodeCap, 4 * pl->list_cap);
   pl->cand_first = 1.5 * est;
@@ -578,6 +624,7 @@ int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, siz
     ca.slot = P<int>(c->slot);
     ca.partial = P<double>(c->partial) + seg * pl.ncon * zsz;
     ca.part0 = 0;
+    ca.sphere = c->sphere;
     CK(c, launch_contract_fp32(ca, pl.ncon, c->st));
   }
   return CTB_OK;
@@ -623,6 +670,8 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   aa.nbins = nb;
   aa.row = c->lay.row;
   std::memcpy(aa.beta, c->beta, sizeof(aa.beta));
+  for (int k = 0; k < 3; ++k) aa.sph_origin[k] = (float)c->origin[k];
+  aa.sph_unit = (float)c->unit;
   double t_stream = 0, t_alm = 0, t_con = 0, t_pack = 0;
   uint64_t pairs = 0, chunks = 0;
   int64_t C = pl.chunk_first;
@@ -674,7 +723,10 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     CK(c, launch_stream(sa, true, pl.stream_blocks, c->st));
     CK(c, cudaEventRecord(ev[2], c->st));
     CK(c, cudaMemsetAsync(work, 0, 8, c->st));
-    CK(c, launch_alm(aa, c->Lk, pl.wpb, pl.alm_blocks, c->st));
+    if (c->sphere)
+      CK(c, launch_am(aa, c->lmax, pl.wpb, pl.alm_blocks, c->st));
+    else
+      CK(c, launch_alm(aa, c->Lk, pl.wpb, pl.alm_blocks, c->st));
     CK(c, cudaEventRecord(ev[3], c->st));
     if (contract) {
       // split the chunk at catalogue boundaries (a batch): each piece adds to its catalogue's partials
@@ -692,7 +744,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
       }
     }
     if (alm_dev_out) {
-      const int ncf = (c->lmax + 1) * (c->lmax + 1);
+      const int ncf = c->sphere ? 2 * c->lmax + 1 : (c->lmax + 1) * (c->lmax + 1);
       const size_t outsz = (size_t)cnt * nb * ncf;
       int blocks = (int)std::min<size_t>((outsz + 255) / 256, 65535);
       k_unpack_alm<<<blocks, 256, 0, c->st>>>(P<float>(c->M), cnt, nb, c->lay.row, P<int>(c->slot), ncf,
@@ -761,7 +813,8 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
   if (tc)
     CK(c, launch_finalize_tc(P<double>(c->partial_tc), c->lmax, pl.ncon, c->nbins, P<double>(c->zeta), c->st));
   else
-    CK(c, launch_finalize(P<double>(c->partial), pl.ncon, c->lmax, c->nbins, P<double>(c->zeta), c->st));
+    CK(c, launch_finalize(P<double>(c->partial), pl.ncon, c->lmax, c->nbins, P<double>(c->zeta), c->sphere != 0,
+                          c->st));
   CK(c, cudaEventRecord(c->ev[evs + 1], c->st));
   const bool dev_out = is_device_ptr(zeta_out);
   CK(c, cudaMemcpyAsync(zeta_out, c->zeta.p, zsz * sizeof(double),
@@ -785,7 +838,7 @@ int compute_impl(ctb_ctx* c, const uint32_t* dprim, int64_t np, double* zeta_out
 int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, const int64_t* n, int k,
                double* zeta_out) {
   if (k < 1 || !xyz || !n || !zeta_out) return fail(c, CTB_ERR_ARG, "batch: k < 1 or NULL argument");
-  if (!c->periodic) return fail(c, CTB_ERR_UNSUPPORTED, "batch mode needs a periodic box");
+  if (!c->periodic || c->sphere) return fail(c, CTB_ERR_UNSUPPORTED, "batch mode needs a periodic box");
   std::vector<int64_t> cum(k + 1, 0);
   int64_t nmax = 0;
   for (int i = 0; i < k; ++i) {
@@ -907,7 +960,7 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
     if (tc)
       CK(c, launch_finalize_tc(pi, c->lmax, pl.ncon, c->nbins, zi, c->st));
     else
-      CK(c, launch_finalize(pi, pl.ncon, c->lmax, c->nbins, zi, c->st));
+      CK(c, launch_finalize(pi, pl.ncon, c->lmax, c->nbins, zi, c->sphere != 0, c->st));
   }
   CK(c, cudaEventRecord(c->ev[11], c->st));
   const bool dev_out = is_device_ptr(zeta_out);
@@ -993,9 +1046,7 @@ int autotune_grid(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
     r = ensure_tables(c);
     if (r) return r;
     // sample size: about 5e8 pairs at the mean density, 256..8192 primaries
-    const double vol = c->periodic ? c->box * c->box * c->box : c->bbox_volume;
-    const double ball = 4.0 / 3.0 * M_PI * (c->rmax * c->rmax * c->rmax - c->rmin * c->rmin * c->rmin);
-    const double per = vol > 0 ? (double)n * std::min(1.0, ball / vol) + 1.0 : 1.0;
+    const double per = mean_neighbours(c) + 1.0;
     const int64_t S = std::min<int64_t>(n, std::max<int64_t>(256, std::min<int64_t>(8192, (int64_t)(5e8 / per))));
     std::vector<uint32_t> sample;
     sample.reserve((size_t)S);
@@ -1028,6 +1079,26 @@ int autotune_grid(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
 extern "C" {
 
 const char* ctb_version(void) { return "ctb 0.1 (sm_103a)"; }
+
+ctb_ctx* ctb_create_sphere(double theta_min, double theta_max, int nbins, int m_max) {
+  if (!std::isfinite(theta_min) || !std::isfinite(theta_max) || !(theta_min >= 0.0) || !(theta_max > theta_min) ||
+      theta_max > M_PI) {
+    g_create_err = "need 0 <= theta_min < theta_max <= pi";
+    return nullptr;
+  }
+  if (m_max < 0 || m_max > CTB_MMAX_CAP) {
+    g_create_err = "m_max out of range [0, 16]";
+    return nullptr;
+  }
+  // open space with the chord limits; bins and the estimator follow the sphere
+  ctb_ctx* c = ctb_create(0.0, 2.0 * std::sin(0.5 * theta_min), 2.0 * std::sin(0.5 * theta_max), nbins, 0);
+  if (!c) return nullptr;
+  c->sphere = 1;
+  c->lmax = m_max;
+  c->tmin = theta_min;
+  c->tmax = theta_max;
+  return c;
+}
 
 ctb_ctx* ctb_create(double box, double r_min, double r_max, int nbins, int ell_max) {
   if (!std::isfinite(box) || !std::isfinite(r_min) || !std::isfinite(r_max)) {
@@ -1127,7 +1198,7 @@ int ctb_get_alm(ctb_ctx* c, const int64_t* primary_idx, int64_t m, float* alm_ou
   PairPlan pl{};
   r = plan_pairs(c, m, &pl);
   if (r) return r;
-  const int nc = (c->lmax + 1) * (c->lmax + 1);
+  const int nc = c->sphere ? 2 * c->lmax + 1 : (c->lmax + 1) * (c->lmax + 1);
   const size_t outsz = (size_t)m * c->nbins * nc;
   const bool dev_out = is_device_ptr(alm_out);
   float* dst = alm_out;
@@ -1160,6 +1231,8 @@ int ctb_set_option(ctb_ctx* c, int key, int64_t v) {
     case CTB_OPT_PRECISION:
       if (v != CTB_PREC_FP32 && v != CTB_PREC_BF16X3 && v != CTB_PREC_TF32)
         return fail(c, CTB_ERR_ARG, "unknown precision");
+      if (c->sphere && v != CTB_PREC_FP32)
+        return fail(c, CTB_ERR_UNSUPPORTED, "the sphere contraction runs in FP32 only");
       c->precision = (int)v;
       return CTB_OK;
     case CTB_OPT_CELLS_PER_RMAX:
@@ -1239,6 +1312,7 @@ int ctb_get_pair_count(ctb_ctx* c, uint64_t* pairs) {
 int ctb_edge_correct(ctb_ctx* c, const double* zeta_nnn, const double* zeta_rrr, double* zeta_out) {
   if (!c) return CTB_ERR_ARG;
   if (!zeta_nnn || !zeta_rrr || !zeta_out) return fail(c, CTB_ERR_ARG, "NULL argument");
+  if (c->sphere) return fail(c, CTB_ERR_UNSUPPORTED, "edge correction of the 3-D multipoles only");
   CK(c, cudaSetDevice(c->dev));
   const int n = c->lmax + 1, nb = c->nbins;
   const size_t zsz = (size_t)n * nb * nb;
@@ -1268,7 +1342,8 @@ int ctb_get_2pcf(ctb_ctx* c, double* out, int cap) {
   std::vector<double> part((size_t)nseg * np * nb);
   CK(c, cudaMemcpyAsync(part.data(), c->pairsum.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  const double s4pi = std::sqrt(4.0 * M_PI);  // a_00 = sum_j w_j / sqrt(4 pi)
+  // a_00 = sum_j w_j / sqrt(4 pi); on the sphere a_0 = sum_j w_j
+  const double s4pi = c->sphere ? 1.0 : std::sqrt(4.0 * M_PI);
   for (int k = 0; k < nseg; ++k)
     for (int b = 0; b < nb; ++b) {
       double s = 0.0;

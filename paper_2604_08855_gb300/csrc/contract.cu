@@ -30,7 +30,7 @@ struct ConShape {
       smem_floats;
 };
 
-__host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row) {
+__host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row, int sphere) {
   ConShape c{};
   c.nbb = (nbins + kConTile - 1) / kConTile;
   c.tiles = c.nbb * (c.nbb + 1) / 2;
@@ -42,7 +42,7 @@ __host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row) {
   if (c.pairs_per_block > c.pairs) c.pairs_per_block = c.pairs;
   c.ny = (c.pairs + c.pairs_per_block - 1) / c.pairs_per_block;
   c.threads = 32 * c.warps_per_pair * c.pairs_per_block;
-  const int nc = (lmax + 1) * (lmax + 1);
+  const int nc = sphere ? 2 * lmax + 1 : (lmax + 1) * (lmax + 1);
   c.per = nc * c.nbb * kConTile;
   c.Q = c.per >= kConStageFloats ? 1 : kConStageFloats / c.per;
   c.red_floats = c.G > 1 ? (c.threads / 32) * 32 * 17 : 0;
@@ -51,11 +51,12 @@ __host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row) {
   return c;
 }
 
-// 4x4 tile of one l: acc[i][j] += w * sum_{m in group} x_i y_j
-__device__ __forceinline__ void con_tile(const float* __restrict__ S, int nbp, int l, int g, int G, int B1, int B2,
-                                         float w, float (&acc)[16]) {
-  const int s0 = l * l;
-  for (int m = g; m <= 2 * l; m += G) {
+// 4x4 tile of one group (a multipole l: components l^2 .. l^2 + 2l; on the
+// sphere, m: component 0, or 2m-1 and 2m): acc[i][j] += w * sum_{c in group} x_i y_j,
+// the lanes of the tile's m-groups taking every G-th component.
+__device__ __forceinline__ void con_tile(const float* __restrict__ S, int nbp, int s0, int nc, int g, int G, int B1,
+                                         int B2, float w, float (&acc)[16]) {
+  for (int m = g; m < nc; m += G) {
     const float4 x = *reinterpret_cast<const float4*>(S + (s0 + m) * nbp + 4 * B1);
     const float4 y = *reinterpret_cast<const float4*>(S + (s0 + m) * nbp + 4 * B2);
     const float xs[4] = {w * x.x, w * x.y, w * x.z, w * x.w};
@@ -66,6 +67,9 @@ __device__ __forceinline__ void con_tile(const float* __restrict__ S, int nbp, i
       for (int j = 0; j < 4; ++j) acc[i * 4 + j] = fmaf(xs[i], ys[j], acc[i * 4 + j]);
   }
 }
+
+__device__ __forceinline__ int group_start(int l, int sphere) { return sphere ? (l == 0 ? 0 : 2 * l - 1) : l * l; }
+__device__ __forceinline__ int group_size(int l, int sphere) { return sphere ? (l == 0 ? 1 : 2) : 2 * l + 1; }
 
 __device__ __forceinline__ void con_flush(const ConShape& sh, const float (&acc)[16], int l, int tile, int g, int B1,
                                           int B2, int nb, int lmax, double* __restrict__ out, float* s_red,
@@ -91,8 +95,9 @@ __device__ __forceinline__ void con_flush(const ConShape& sh, const float (&acc)
 
 __global__ void __launch_bounds__(kConMaxThreads, 1) k_contract_fp32(ContractArgs a) {
   extern __shared__ float s_dyn[];
-  const int nb = a.nbins, L = a.lmax, nc = (L + 1) * (L + 1);
-  const ConShape sh = con_shape(nb, L, a.row);
+  const int nb = a.nbins, L = a.lmax;
+  const int nc = a.sphere ? 2 * L + 1 : (L + 1) * (L + 1);  // coefficients per (primary, bin)
+  const ConShape sh = con_shape(nb, L, a.row, a.sphere);
   const int nbp = sh.nbb * kConTile;
   const int per = sh.per;
   // [row slot -> coefficient table | Q staged primaries | per-warp m-group combine buffers]
@@ -162,8 +167,9 @@ __global__ void __launch_bounds__(kConMaxThreads, 1) k_contract_fp32(ContractArg
       for (int q = 0; q < cnt; ++q) {
         const float w = a.wprim[pb + q];
         const float* S = s_rows + q * per;
-        con_tile(S, nbp, la, g, sh.G, B1, B2, w, acc_a);
-        if (lb != la) con_tile(S, nbp, lb, g, sh.G, B1, B2, w, acc_b);
+        con_tile(S, nbp, group_start(la, a.sphere), group_size(la, a.sphere), g, sh.G, B1, B2, w, acc_a);
+        if (lb != la)
+          con_tile(S, nbp, group_start(lb, a.sphere), group_size(lb, a.sphere), g, sh.G, B1, B2, w, acc_b);
       }
     }
   }
@@ -175,8 +181,8 @@ __global__ void __launch_bounds__(kConMaxThreads, 1) k_contract_fp32(ContractArg
 }
 
 // Resident blocks per SM of the contraction for this shape (0 if it cannot run).
-int contract_fp32_blocks_per_sm(int nbins, int lmax, int row) {
-  const ConShape sh = con_shape(nbins, lmax, row);
+int contract_fp32_blocks_per_sm(int nbins, int lmax, int row, int sphere) {
+  const ConShape sh = con_shape(nbins, lmax, row, sphere);
   const size_t smem = (size_t)sh.smem_floats * sizeof(float);
   if (smem > 200 * 1024) return 0;
   if (cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -188,7 +194,7 @@ int contract_fp32_blocks_per_sm(int nbins, int lmax, int row) {
 
 cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t st) {
   if (a.np == 0) return cudaSuccess;
-  const ConShape sh = con_shape(a.nbins, a.lmax, a.row);
+  const ConShape sh = con_shape(a.nbins, a.lmax, a.row, a.sphere);
   const size_t smem = (size_t)sh.smem_floats * sizeof(float);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -198,8 +204,9 @@ cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t
   return cudaGetLastError();
 }
 
-// zeta_l(b1,b2) = 4 pi/(2l+1) * sum_parts partial[part][l][min b][max b], in part order.
-__global__ void k_finalize(const double* __restrict__ partial, int nparts, int lmax, int nb,
+// zeta_l(b1,b2) = f_l * sum_parts partial[part][l][min b][max b], in part
+// order; f_l = 4 pi/(2l+1) for the 3-D multipoles, 1 on the sphere.
+__global__ void k_finalize(const double* __restrict__ partial, int nparts, int lmax, int nb, int sphere,
                            double* __restrict__ zeta) {
   const int total = (lmax + 1) * nb * nb;
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < total; o += gridDim.x * blockDim.x) {
@@ -214,15 +221,15 @@ __global__ void k_finalize(const double* __restrict__ partial, int nparts, int l
     const size_t stride = (size_t)(lmax + 1) * nb * nb;
     double s = 0.0;
     for (int p = 0; p < nparts; ++p) s += partial[(size_t)p * stride + idx];
-    zeta[o] = s * (4.0 * 3.14159265358979323846 / (2.0 * l + 1.0));
+    zeta[o] = sphere ? s : s * (4.0 * 3.14159265358979323846 / (2.0 * l + 1.0));
   }
 }
 
-cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbins, double* zeta,
+cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbins, double* zeta, bool sphere,
                             cudaStream_t st) {
   const int total = (lmax + 1) * nbins * nbins;
   const int blocks = (total + 255) / 256;
-  k_finalize<<<blocks, 256, 0, st>>>(partial, nparts, lmax, nbins, zeta);
+  k_finalize<<<blocks, 256, 0, st>>>(partial, nparts, lmax, nbins, sphere ? 1 : 0, zeta);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -44,6 +44,9 @@ struct Geom {
   float inv_dr_u;      // nbins / (r_max - r_min) in 1/units
   float rcell;         // r_max in cell units, padded by a small slack
   float cell_scale;    // nc / 2^shift : units -> cell units
+  int general;         // 1: bin edges not linear in r (sphere: chords of linear angles);
+                       //    rmin_u / inv_dr_u give only a first guess, the exact
+                       //    thresholds decide every candidate
 };
 
 // Rows of the neighbour scan: W x W x-rows of cells at (dy, dz) offsets
@@ -232,9 +235,14 @@ struct AlmArgs {
   unsigned long long* work;
   int nbins;
   int row;
+  float sph_origin[3];            // sphere mode: the points' position = origin + unit * (x, y, z)
+  float sph_unit;
   float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];  // recurrence beta_lm at [l*(kLmaxCap+1)+m]
 };
 int alm_blocks_per_sm(int lmax_kernel, int warps_per_block);
+// sphere.cu: projected multipoles m = 0..mmax (mmax <= CTB_MMAX_CAP)
+int am_blocks_per_sm(int mmax, int warps_per_block);
+cudaError_t launch_am(const AlmArgs& a, int mmax, int warps_per_block, int nblocks, cudaStream_t st);
 cudaError_t launch_alm(const AlmArgs& a, int lmax_kernel, int warps_per_block, int nblocks, cudaStream_t st);
 
 // contract.cu
@@ -248,9 +256,10 @@ struct ContractArgs {
   const int* slot;         // device copy of Layout::slot
   double* partial;         // [nparts][(lmax+1)][nbins][nbins] (upper triangle used)
   int part0;               // first partial row this launch writes
+  int sphere;              // 0: group l = components l^2 .. l^2+2l; 1: group m = {0} or {2m-1, 2m}
 };
 cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t st);
-int contract_fp32_blocks_per_sm(int nbins, int lmax, int row);
+int contract_fp32_blocks_per_sm(int nbins, int lmax, int row, int sphere);
 
 // edge.cu
 void make_threej_table(int lmax, std::vector<double>& t);  // (a b c; 0 0 0)^2, [a][b][c], a,b,c <= lmax
@@ -259,8 +268,8 @@ cudaError_t launch_edge_correct(const double* zn, const double* zr, const double
 // partial[part][b] += sum over a fixed slice of the primaries of w_p * M[p][b][col]
 cudaError_t launch_pair_sums(const float* M, const float* w, int64_t np, int nbins, int row, int col,
                              double* partial, int nparts, cudaStream_t st);
-cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbins,
-                            double* zeta, cudaStream_t st);
+cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbins, double* zeta, bool sphere,
+                            cudaStream_t st);
 
 // contract_tc.cu -- tcgen05 contraction (BF16 hi/lo split or TF32)
 int tc_npad(int nbins);

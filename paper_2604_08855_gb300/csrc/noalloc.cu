@@ -98,7 +98,7 @@ extern "C" int ctb_contract_noalloc(const float* alm, const float* w, int64_t np
     e = launch_contract_fp32(ca, kNoallocParts, st);
     if (e != cudaSuccess) return CTB_ERR_CUDA;
   }
-  e = launch_finalize(sc.partial, kNoallocParts, ell_max, nbins, zeta_out, st);
+  e = launch_finalize(sc.partial, kNoallocParts, ell_max, nbins, zeta_out, false, st);
   if (e != cudaSuccess) return CTB_ERR_CUDA;
   return CTB_OK;
 }

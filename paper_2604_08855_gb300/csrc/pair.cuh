@@ -223,13 +223,31 @@ __device__ __forceinline__ Prefetch prefetch_start(const uint32_t* lists, const 
   return pf;
 }
 
-// Accumulate one m-range pass over one run and store it to the row; the
-// loads for the first iterations of `nxt` are issued inside the loop, so the
-// next run starts without a memory bubble.
+// The per-neighbour work of one m-range pass of the 3-D harmonics: the unit
+// direction, then the pass's recurrences and one FMA per coefficient.
 template <int L, int M0, int M1>
-__device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, const uint4 P, Prefetch& pf,
-                                         float* __restrict__ out, int base, float* sbuf, int lane, uint32_t pe) {
-  constexpr int NCP = round32(coef_count(L, M0, M1));
+struct Step3D {
+  static constexpr int NCP = round32(coef_count(L, M0, M1));
+  // Only kernels with a single m-pass take the full-lane copy of the step:
+  // with several passes the extra code no longer fits the instruction cache.
+  static constexpr bool kFullLaneLoop = pass_end(L, 0, pass_cap(L, 0)) >= L;
+  const AlmArgs& a;
+  __device__ __forceinline__ void operator()(float* acc, float w, float dx, float dy, float dz) const {
+    const float ir = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    accum_pass<L, M0, M1>(a, acc, w, dx * ir, dy * ir, dz * ir);
+  }
+};
+
+// Accumulate one pass over one run and store it to the row; the loads for
+// the first iterations of `nxt` are issued inside the loop, so the next run
+// starts without a memory bubble.  `step` adds one neighbour (weight and
+// separation in units; a lane without a neighbour passes w = 0) to the
+// Step::NCP accumulators.
+template <class Step>
+__device__ __forceinline__ void run_steps(const AlmArgs& a, const Step& step, Run cur, Run nxt, const uint4 P,
+                                          Prefetch& pf, float* __restrict__ out, int base, float* sbuf, int lane,
+                                          uint32_t pe) {
+  constexpr int NCP = Step::NCP;
   const uint32_t* __restrict__ lists = a.lists;
   const uint4* __restrict__ pts = a.pts;
   float acc[NCP];
@@ -243,7 +261,7 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
   // Steps whose lanes all hold a neighbour and whose look-ahead words are in
   // this run: no validity tests, no run switch.  (The list buffer has slack
   // past its last entry, so the L2 prefetch needs no bound here.)
-  {
+  if constexpr (Step::kFullLaneLoop) {
     const uint32_t full = cur.n >> 5;
     if (t + 3u < full) {
       // two gathers in flight: q0 = point(t), q1 = point(t + 1), j1 = word(t + 2)
@@ -264,8 +282,7 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
         const float dx = __int2float_rn((int)(q.x - P.x));
         const float dy = __int2float_rn((int)(q.y - P.y));
         const float dz = __int2float_rn((int)(q.z - P.z));
-        const float ir = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        accum_pass<L, M0, M1>(a, acc, __uint_as_float(q.w), dx * ir, dy * ir, dz * ir);
+        step(acc, __uint_as_float(q.w), dx, dy, dz);
       }
       // back to one gather in flight: q0 = point(t) (valid), j1 = word(t + 1)
       pf.j0 = 0u;
@@ -291,8 +308,7 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
       dz = 0.f;
       w = 0.f;
     }
-    const float ir = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    accum_pass<L, M0, M1>(a, acc, w, dx * ir, dy * ir, dz * ir);
+    step(acc, w, dx, dy, dz);
   }
   smem_transpose_reduce<NCP>(acc, sbuf, lane);
   // lane holds the warp totals of local slots [lane * V, lane * V + V); turn
@@ -321,7 +337,14 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
   }
 }
 
-// The m-range passes of one bin; the last pass prefetches the next bin's run.
+template <int L, int M0, int M1>
+__device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, const uint4 P, Prefetch& pf,
+                                         float* __restrict__ out, int base, float* sbuf, int lane, uint32_t pe) {
+  run_steps(a, Step3D<L, M0, M1>{a}, cur, nxt, P, pf, out, base, sbuf, lane, pe);
+}
+
+// The m-range passes of one bin (bin-major: a bin's run is re-read by each
+// pass while it is still in L1); the last pass prefetches the next bin's run.
 template <int L, int M0, int BASE>
 struct PassChain {
   static constexpr int M1 = pass_end(L, M0, pass_cap(L, M0));
@@ -355,8 +378,8 @@ constexpr size_t alm_smem_per_warp() {
 }
 
 // One warp per primary: its (primary, bin) lists are consecutive runs of the
-// lists buffer; each list is accumulated in registers and flushed once, with
-// the next list's first loads already in flight.
+// lists buffer; each list is accumulated in registers and flushed once per
+// m-pass, with the next list's first loads already in flight.
 template <int L>
 __global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
   extern __shared__ float s_alm[];

@@ -243,8 +243,10 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
               const float tt = (r - g.rmin_u) * g.inv_dr_u;
               b = (int)floorf(tt);
               const float fr = tt - (float)b;
-              if (b < 0 || b >= nbins || fr < 1e-4f || fr > 1.f - 1e-4f) {
-                // within float rounding of an edge: exact integer r^2 vs exact thresholds
+              if (g.general || b < 0 || b >= nbins || fr < 1e-4f || fr > 1.f - 1e-4f) {
+                // within float rounding of an edge (or edges not linear in r,
+                // where b is only a first guess): exact integer r^2 vs exact
+                // thresholds
                 const unsigned long long e2 = (unsigned long long)((long long)ix * ix + (long long)iy * iy +
                                                                    (long long)iz * iz);
                 if (e2 == 0ull || e2 < __ldg(a.thr) || e2 >= __ldg(a.thr + nbins)) {

@@ -26,10 +26,10 @@ OPT_PRECISION, OPT_CELLS_PER_RMAX, OPT_LIST_CAPACITY, OPT_WARPS_PER_BLOCK, OPT_C
     OPT_DETERMINISTIC, OPT_AUTOTUNE, OPT_FAULT_INJECT = 1, 2, 3, 4, 5, 6, 7, 8
 INJECT_STALL, INJECT_ALLOC = 1, 2
 PREC_FP32, PREC_BF16X3, PREC_TF32 = 0, 1, 2
-LMAX_CAP, NBINS_CAP = 20, 64
+LMAX_CAP, NBINS_CAP, MMAX_CAP = 20, 64, 16
 
 # every symbol include/ctb.h declares
-EXPORTS = ("ctb_create", "ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm",
+EXPORTS = ("ctb_create", "ctb_create_sphere", "ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm",
            "ctb_compute_batch", "ctb_set_option", "ctb_set_stream", "ctb_set_allocator",
            "ctb_get_timings", "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_grid",
            "ctb_get_2pcf", "ctb_edge_correct", "ctb_get_launch_count", "ctb_contract_noalloc", "ctb_destroy", "ctb_last_error", "ctb_version")
@@ -54,6 +54,8 @@ def load(path: str | None = None):
     lib = ctypes.CDLL(path)
     vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     lib.ctb_create.argtypes = [d, d, d, i32, i32]
+    lib.ctb_create_sphere.argtypes = [d, d, i32, i32]
+    lib.ctb_create_sphere.restype = vp
     lib.ctb_create.restype = vp
     lib.ctb_set_points.argtypes = [vp, vp, vp, i64]
     lib.ctb_compute.argtypes = [vp, vp]
@@ -106,17 +108,37 @@ def _as_f64(x, shape_tail=None):
 
 
 class CTB:
-    """One estimator configuration on the current CUDA device."""
+    """One estimator configuration on the current CUDA device.
 
-    def __init__(self, box: float, rmin: float, rmax: float, nbins: int, lmax: int):
+    CTB(box, rmin, rmax, nbins, lmax): 3-D Legendre multipoles (box <= 0: open).
+    CTB.sphere(theta_min, theta_max, nbins, mmax): projected multipoles on the
+    unit sphere (ctb_create_sphere); ``lmax`` then holds m_max.
+    """
+
+    def __init__(self, box: float, rmin: float, rmax: float, nbins: int, lmax: int, _sphere: bool = False):
         self.lib = load()
         self.box, self.rmin, self.rmax, self.nbins, self.lmax = float(box), float(rmin), float(rmax), int(nbins), int(lmax)
-        h = self.lib.ctb_create(self.box, self.rmin, self.rmax, self.nbins, self.lmax)
+        self.is_sphere = bool(_sphere)
+        if self.is_sphere:
+            h = self.lib.ctb_create_sphere(self.rmin, self.rmax, self.nbins, self.lmax)
+        else:
+            h = self.lib.ctb_create(self.box, self.rmin, self.rmax, self.nbins, self.lmax)
         if not h:
             raise CTBError(ERR_ARG, self.lib.ctb_last_error(None).decode())
         self._h = ctypes.c_void_p(h)
         self.n = None
         self._keep = []
+
+    @classmethod
+    def sphere(cls, theta_min: float, theta_max: float, nbins: int, mmax: int):
+        """Projected multipoles zeta_m, m = 0..mmax, of directions on the unit
+        sphere, bins linear in the angle [theta_min, theta_max) (radians)."""
+        return cls(0.0, theta_min, theta_max, nbins, mmax, _sphere=True)
+
+    @property
+    def ncoef(self) -> int:
+        """Coefficients per (primary, bin) of get_alm."""
+        return 2 * self.lmax + 1 if self.is_sphere else (self.lmax + 1) ** 2
 
     def close(self):
         if getattr(self, "_h", None):
@@ -203,7 +225,7 @@ class CTB:
 
     def get_alm(self, primaries, out=None):
         p = primaries if hasattr(primaries, "data_ptr") else np.ascontiguousarray(primaries, dtype=np.int64)
-        a = self._out(out, (int(p.shape[0]), self.nbins, (self.lmax + 1) ** 2), np.float32)
+        a = self._out(out, (int(p.shape[0]), self.nbins, self.ncoef), np.float32)
         self._check(self.lib.ctb_get_alm(self._h, _ptr(p), int(p.shape[0]), _ptr(a)))
         return a
 

@@ -187,3 +187,60 @@ def sample_primaries(n: int, k: int, seed: int = 7):
     """k distinct primary indices out of n, seeded, sorted."""
     k = min(k, n)
     return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False)).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# the unit sphere (projected fields)
+
+
+def fibonacci_sphere(n: int) -> np.ndarray:
+    """n directions on the golden-angle spiral: equal-area and near-uniform,
+    standing in for the pixel centres of a HEALPix map with n pixels.
+    Snapped to the 2^-20 dyadic grid (so not exactly unit length)."""
+    k = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * k / n
+    phi = k * (np.pi * (3.0 - np.sqrt(5.0)))
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return snap_dyadic(np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1))
+
+
+def sphere_cap(n: int, seed: int, theta_cap: float = 0.3, centre=(0.2, -0.3, 0.93)) -> np.ndarray:
+    """n random directions uniform in a spherical cap (snapped to 2^-20)."""
+    rng = np.random.default_rng(seed)
+    c = np.asarray(centre, dtype=np.float64)
+    c /= np.linalg.norm(c)
+    mu = rng.uniform(np.cos(theta_cap), 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * np.pi, n)
+    s = np.sqrt(1.0 - mu * mu)
+    local = np.stack([s * np.cos(ph), s * np.sin(ph), mu], axis=1)
+    z = np.array([0.0, 0.0, 1.0])
+    v = np.cross(z, c)
+    sn, cs = np.linalg.norm(v), float(z @ c)
+    if sn > 1e-12:
+        k = v / sn
+        K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        local = local @ (np.eye(3) + sn * K + (1 - cs) * K @ K).T
+    return snap_dyadic(local)
+
+
+def sphere_field(xyz: np.ndarray, seed: int, nblobs: int = 64, width: float = 0.05, noise: float = 0.1):
+    """A smooth random scalar field at the given directions (a stand-in for a
+    convergence map): von Mises blobs of random sign and amplitude plus white
+    noise.  These are the weights of the projected estimator."""
+    rng = np.random.default_rng(seed)
+    cen = rng.normal(size=(nblobs, 3))
+    cen /= np.linalg.norm(cen, axis=1)[:, None]
+    amp = rng.normal(size=nblobs)
+    kappa = 1.0 / (width * width)
+    f = np.zeros(xyz.shape[0])
+    for i0 in range(0, xyz.shape[0], 1 << 20):
+        x = xyz[i0:i0 + (1 << 20)]
+        f[i0:i0 + x.shape[0]] = np.exp(kappa * (x @ cen.T - 1.0)) @ amp
+    return f + noise * rng.normal(size=xyz.shape[0])
+
+
+def sphere_map(nside: int, seed: int = 11):
+    """A full-sky map with 12 nside^2 pixels (Fibonacci directions) and a
+    smooth random field as pixel values."""
+    xyz = fibonacci_sphere(12 * nside * nside)
+    return xyz, sphere_field(xyz, seed)
