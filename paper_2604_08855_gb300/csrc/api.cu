@@ -347,7 +347,8 @@ void finish_geom(ctb_ctx* c, Geom& g, uint32_t nc) {
   g.nc = nc;
   g.ncells = nc * nc * nc;
   const double rmin_u = c->rmin / c->unit, rmax_u = c->rmax / c->unit;
-  g.rlo2_u = (float)(rmin_u * rmin_u * (1.0 - 1e-5));
+  // the float pre-filter; never 0, so that it also rejects r = 0
+  g.rlo2_u = std::max((float)(rmin_u * rmin_u * (1.0 - 1e-5)), 0.25f);
   g.rhi2_u = (float)(rmax_u * rmax_u * (1.0 + 1e-5));
   g.rmin_u = (float)rmin_u;
   g.inv_dr_u = (float)(c->nbins / (rmax_u - rmin_u));
@@ -469,7 +470,7 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   CK(c, ensure(c, c->cell_start, ((size_t)g.ncells + 1) * 4));
   const size_t hw = sort_hist_words(n);
   CK(c, ensure(c, c->hist, hw * 4));
-  CK(c, ensure(c, c->scan_tmp, scan_tmp_words(hw) * 4));
+  CK(c, ensure(c, c->scan_tmp, std::max(scan_tmp_words(hw), scan_tmp_words((size_t)g.ncells + 1)) * 4));
 
   IngestOut io{P<uint32_t>(c->key0), P<uint32_t>(c->val0), P<uint4>(c->pts_in)};
   const double inv_unit = 1.0 / c->unit;
@@ -484,7 +485,7 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   uint32_t* vs = in1 ? sb.v1 : sb.v0;
   CK(c, launch_gather(vs, P<uint4>(c->pts_in), n, P<uint4>(c->pts), P<uint32_t>(c->s2i), P<uint32_t>(c->i2s),
                       c->st));
-  CK(c, launch_cell_start(ks, n, g.ncells, P<uint32_t>(c->cell_start), c->st));
+  CK(c, launch_cell_start(ks, n, g.ncells, P<uint32_t>(c->cell_start), P<uint32_t>(c->scan_tmp), c->st));
   CK(c, cudaEventRecord(c->ev[2], c->st));
   uint32_t fl = 0;
   CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
@@ -605,7 +606,7 @@ int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, siz
     CK(c, ensure(c, c->kp_d, kp.size() * 8));
     CK(c, cudaMemcpyAsync(c->lbase_d.p, lb.data(), lb.size() * 8, cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemcpyAsync(c->kp_d.p, kp.data(), kp.size() * 8, cudaMemcpyHostToDevice, c->st));
-    CK(c, launch_pack(tf32, M, wp, cnt, nb, c->lay.row, P<int>(c->slot_lm), P<unsigned long long>(c->lbase_d),
+    CK(c, launch_pack(tf32, M, wp, cnt, nb, c->lay.row, c->lmax, P<int>(c->slot), P<unsigned long long>(c->lbase_d),
                       P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p, c->ops[2].p, c->ops[3].p, c->st));
     CK(c, cudaEventRecord(*ev_pack, c->st));
     CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), c->ops[0].p, c->ops[1].p, c->ops[2].p,
@@ -886,7 +887,7 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   CK(c, ensure(c, c->cell_start, (size_t)(cells_all + 1) * 4));
   const size_t hw = sort_hist_words(N);
   CK(c, ensure(c, c->hist, hw * 4));
-  CK(c, ensure(c, c->scan_tmp, scan_tmp_words(hw) * 4));
+  CK(c, ensure(c, c->scan_tmp, std::max(scan_tmp_words(hw), scan_tmp_words((size_t)cells_all + 1)) * 4));
   CK(c, ensure(c, c->flags, 64));
   CK(c, cudaMemsetAsync(c->flags.p, 0, 64, c->st));
   CK(c, cudaEventRecord(c->ev[0], c->st));
@@ -918,7 +919,7 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   uint32_t* ks = in1 ? sb.k1 : sb.k0;
   uint32_t* vs = in1 ? sb.v1 : sb.v0;
   CK(c, launch_gather(vs, P<uint4>(c->pts_in), N, P<uint4>(c->pts), P<uint32_t>(c->s2i), P<uint32_t>(c->i2s), c->st));
-  CK(c, launch_cell_start(ks, N, (uint32_t)cells_all, P<uint32_t>(c->cell_start), c->st));
+  CK(c, launch_cell_start(ks, N, (uint32_t)cells_all, P<uint32_t>(c->cell_start), P<uint32_t>(c->scan_tmp), c->st));
   CK(c, cudaEventRecord(c->ev[2], c->st));
   uint32_t fl = 0;
   CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));

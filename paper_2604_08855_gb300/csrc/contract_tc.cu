@@ -330,42 +330,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
 // ---------------------------------------------------------------------------
 // pack: coefficient rows -> K-major operands per l
 
-// slot_lm[s] = l * 64 + (m + l) for the slots of l <= lmax, -1 otherwise
+// A block takes kPackPrims consecutive primaries.  For each bin it stages
+// their rows in shared memory (coalesced row reads), then writes, for each l,
+// the operands of those primaries: a contiguous span of kPackPrims * (2l+1)
+// elements of the (l, bin) region, in coalesced stores.  A = w_p a and B = a,
+// each as a BF16 hi + lo pair (or rounded to TF32).
+constexpr int kPackPrims = 16;
+constexpr int kPackThreads = 256;
+
 template <bool TF32>
-__global__ void k_pack(const float* __restrict__ M, const float* __restrict__ wprim, int64_t np, int nbins, int row,
-                       const int* __restrict__ slot_lm, const unsigned long long* __restrict__ lbase,
-                       const unsigned long long* __restrict__ kp, void* __restrict__ outA_hi,
-                       void* __restrict__ outA_lo, void* __restrict__ outB_hi, void* __restrict__ outB_lo) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nrows = np * nbins;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t rw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); rw < nrows; rw += warps) {
-    const int64_t p = rw / nbins;
-    const int b = (int)(rw % nbins);
-    const float wp = __ldg(wprim + p);
-    const float* src = M + rw * row;
-    for (int s = lane; s < row; s += 32) {
-      const int lm = __ldg(slot_lm + s);
-      if (lm < 0) continue;
-      const int l = lm >> 6, mi = lm & 63;
-      const float v = __ldcs(src + s);
-      const unsigned long long idx = lbase[l] + (unsigned long long)b * kp[l] + (unsigned long long)p * (2 * l + 1) + mi;
-      const float av = wp * v;
-      if (TF32) {
-        uint32_t ta, tb;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta) : "f"(av));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb) : "f"(v));
-        reinterpret_cast<uint32_t*>(outA_hi)[idx] = ta;
-        reinterpret_cast<uint32_t*>(outB_hi)[idx] = tb;
-      } else {
-        const __nv_bfloat16 ah = __float2bfloat16_rn(av);
-        const __nv_bfloat16 al = __float2bfloat16_rn(av - __bfloat162float(ah));
-        const __nv_bfloat16 bh = __float2bfloat16_rn(v);
-        const __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(bh));
-        reinterpret_cast<__nv_bfloat16*>(outA_hi)[idx] = ah;
-        reinterpret_cast<__nv_bfloat16*>(outA_lo)[idx] = al;
-        reinterpret_cast<__nv_bfloat16*>(outB_hi)[idx] = bh;
-        reinterpret_cast<__nv_bfloat16*>(outB_lo)[idx] = bl;
+__global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__ M, const float* __restrict__ wprim,
+                                                       int64_t np, int nbins, int row, int lmax,
+                                                       const int* __restrict__ slot,
+                                                       const unsigned long long* __restrict__ lbase,
+                                                       const unsigned long long* __restrict__ kp,
+                                                       void* __restrict__ outA_hi, void* __restrict__ outA_lo,
+                                                       void* __restrict__ outB_hi, void* __restrict__ outB_lo) {
+  extern __shared__ float s_pack[];
+  float* rows = s_pack;                          // [kPackPrims][row]
+  float* s_w = rows + kPackPrims * row;          // [kPackPrims]
+  int* s_slot = reinterpret_cast<int*>(s_w + kPackPrims);  // [(lmax+1)^2]
+  const int nc = (lmax + 1) * (lmax + 1);
+  const int64_t p0 = (int64_t)blockIdx.x * kPackPrims;
+  const int pt = (int)min((int64_t)kPackPrims, np - p0);
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) s_slot[c] = slot[c];
+  for (int q = threadIdx.x; q < pt; q += blockDim.x) s_w[q] = __ldg(wprim + p0 + q);
+  for (int b = 0; b < nbins; ++b) {
+    __syncthreads();  // the previous bin's rows are consumed (and the tables on entry)
+    for (int q = 0; q < pt; ++q) {
+      const float* src = M + ((p0 + q) * nbins + b) * (int64_t)row;
+      for (int c = threadIdx.x; c < row; c += blockDim.x) rows[q * row + c] = __ldcs(src + c);
+    }
+    __syncthreads();
+    for (int l = 0; l <= lmax; ++l) {
+      const int nl = 2 * l + 1;
+      const float inv = 1.f / (float)nl;
+      const unsigned long long base = lbase[l] + (unsigned long long)b * kp[l] + (unsigned long long)p0 * nl;
+      const int count = pt * nl;
+      for (int e = threadIdx.x; e < count; e += blockDim.x) {
+        const int q = (int)(((float)e + 0.5f) * inv);  // e / nl, exact for these sizes
+        const int mi = e - q * nl;
+        const float v = rows[q * row + s_slot[l * l + mi]];
+        const float av = s_w[q] * v;
+        const unsigned long long idx = base + (unsigned long long)e;
+        if (TF32) {
+          uint32_t ta, tb;
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta) : "f"(av));
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb) : "f"(v));
+          reinterpret_cast<uint32_t*>(outA_hi)[idx] = ta;
+          reinterpret_cast<uint32_t*>(outB_hi)[idx] = tb;
+        } else {
+          const __nv_bfloat16 ah = __float2bfloat16_rn(av);
+          const __nv_bfloat16 al = __float2bfloat16_rn(av - __bfloat162float(ah));
+          const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+          const __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(bh));
+          reinterpret_cast<__nv_bfloat16*>(outA_hi)[idx] = ah;
+          reinterpret_cast<__nv_bfloat16*>(outA_lo)[idx] = al;
+          reinterpret_cast<__nv_bfloat16*>(outB_hi)[idx] = bh;
+          reinterpret_cast<__nv_bfloat16*>(outB_lo)[idx] = bl;
+        }
       }
     }
   }
@@ -424,16 +447,24 @@ void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned 
   *elems = (size_t)acc;
 }
 
-cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row,
-                        const int* slot_lm, const unsigned long long* lbase, const unsigned long long* kp,
-                        void* ahi, void* alo, void* bhi, void* blo, cudaStream_t st) {
+cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row, int lmax,
+                        const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* ahi,
+                        void* alo, void* bhi, void* blo, cudaStream_t st) {
   if (np == 0) return cudaSuccess;
-  const int64_t rows = np * nbins;
-  int blocks = (int)std::min<int64_t>((rows + 7) / 8, 65535);
-  if (tf32)
-    k_pack<true><<<blocks, 256, 0, st>>>(M, wprim, np, nbins, row, slot_lm, lbase, kp, ahi, alo, bhi, blo);
-  else
-    k_pack<false><<<blocks, 256, 0, st>>>(M, wprim, np, nbins, row, slot_lm, lbase, kp, ahi, alo, bhi, blo);
+  const int64_t blocks = (np + kPackPrims - 1) / kPackPrims;
+  const size_t smem = ((size_t)kPackPrims * row + kPackPrims + (size_t)(lmax + 1) * (lmax + 1)) * 4;
+  cudaError_t e;
+  if (tf32) {
+    e = cudaFuncSetAttribute(k_pack<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_pack<true><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, ahi,
+                                                               alo, bhi, blo);
+  } else {
+    e = cudaFuncSetAttribute(k_pack<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_pack<false><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, ahi,
+                                                                alo, bhi, blo);
+  }
   ++g_launches;
   return cudaGetLastError();
 }

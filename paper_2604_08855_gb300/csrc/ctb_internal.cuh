@@ -191,8 +191,10 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, size_t len,
 cudaError_t launch_gather(const uint32_t* val_sorted, const uint4* pts_in, int64_t n,
                           uint4* pts_sorted, uint32_t* sorted_to_input,
                           uint32_t* input_to_sorted, cudaStream_t st);
-cudaError_t launch_cell_start(const uint32_t* key_sorted, int64_t n, uint32_t ncells,
-                              uint32_t* cell_start, cudaStream_t st);
+// cell_start[c] = first sorted position with key >= c, c in [0, ncells];
+// scan_tmp holds scan_tmp_words(ncells + 1) words
+cudaError_t launch_cell_start(const uint32_t* key_sorted, int64_t n, uint32_t ncells, uint32_t* cell_start,
+                              uint32_t* scan_tmp, cudaStream_t st);
 
 // stream.cu -- neighbour enumeration (count pass, then fill pass)
 struct StreamArgs {
@@ -275,9 +277,10 @@ cudaError_t launch_finalize(const double* partial, int nparts, int lmax, int nbi
 int tc_npad(int nbins);
 void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned long long>& lbase,
                std::vector<unsigned long long>& kp, size_t* elems);
-cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row,
-                        const int* slot_lm, const unsigned long long* lbase, const unsigned long long* kp,
-                        void* ahi, void* alo, void* bhi, void* blo, cudaStream_t st);
+// slot: the layout's slot of coefficient l*l+l+m (l <= lmax)
+cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row, int lmax,
+                        const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* ahi,
+                        void* alo, void* bhi, void* blo, cudaStream_t st);
 cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const unsigned long long* h_lbase,
                                const unsigned long long* h_kp, void* ahi, void* alo, void* bhi, void* blo,
                                double* partial, int nsplit, unsigned int* err, bool inject_stall,

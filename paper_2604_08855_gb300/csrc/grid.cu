@@ -340,24 +340,38 @@ cudaError_t launch_gather(const uint32_t* val_sorted, const uint4* pts_in, int64
   return cudaGetLastError();
 }
 
-// cell_start[c] = first sorted position with key >= c, for c in [0, ncells]
-__global__ void k_cell_start(const uint32_t* __restrict__ key, int64_t n, uint32_t ncells,
-                             uint32_t* __restrict__ cs) {
+// cell_start[c] = first sorted position with key >= c, for c in [0, ncells]:
+// the exclusive prefix sum of the points per cell.  The counts are added by
+// one atomic per run of equal keys within a warp (the keys are sorted), so
+// empty cells cost only the scan, however long the empty stretches.
+__global__ void k_cell_count(const uint32_t* __restrict__ key, int64_t n, uint32_t* __restrict__ cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
-    int64_t cur = i < n ? (int64_t)key[i] : (int64_t)ncells;
-    int64_t prev = i > 0 ? (int64_t)key[i - 1] : -1;
-    for (int64_t c = prev + 1; c <= cur; ++c) cs[c] = (uint32_t)i;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + (threadIdx.x & ~31) + lane;
+    const bool ok = i < n;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const uint32_t k = key[i];
+      const unsigned grp = __match_any_sync(act, k);
+      if (lane == __ffs(grp) - 1) atomicAdd(cnt + k, (uint32_t)__popc(grp));
+    }
   }
 }
 
 cudaError_t launch_cell_start(const uint32_t* key_sorted, int64_t n, uint32_t ncells, uint32_t* cell_start,
-                              cudaStream_t st) {
-  int blocks = (int)((n + 1 + 255) / 256);
-  if (blocks > 65535 * 4) blocks = 65535 * 4;
-  k_cell_start<<<blocks, 256, 0, st>>>(key_sorted, n, ncells, cell_start);
-  ++g_launches;
-  return cudaGetLastError();
+                              uint32_t* scan_tmp, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(cell_start, 0, ((size_t)ncells + 1) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 65535 * 4) blocks = 65535 * 4;
+    k_cell_count<<<blocks, 256, 0, st>>>(key_sorted, n, cell_start);
+    ++g_launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return exclusive_scan_u32(cell_start, cell_start, (size_t)ncells + 1, scan_tmp, st);
 }
 
 }  // namespace ctb

@@ -232,18 +232,20 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
           for (uint32_t base = cs; base < ce; base += 32) {
             const uint32_t j = base + lane;
             const bool valid = j < ce;
-            const uint4 q = valid ? __ldg(a.pts + j) : P;
+            // lanes past the segment load its last point and are masked by `valid`
+            const uint4 q = __ldg(a.pts + (valid ? j : ce - 1u));
             const int ix = (int)(q.x - P.x), iy = (int)(q.y - P.y), iz = (int)(q.z - P.z);
             const float dx = __int2float_rn(ix), dy = __int2float_rn(iy), dz = __int2float_rn(iz);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool inb = valid && r2 > 0.f && r2 >= g.rlo2_u && r2 < g.rhi2_u;
+            // rlo2_u > 0 also excludes r = 0 (coincident points)
+            bool inb = valid && r2 >= g.rlo2_u && r2 < g.rhi2_u;
             int b = 0;
             if (inb) {
               const float r = r2 * rsqrtf(r2);
               const float tt = (r - g.rmin_u) * g.inv_dr_u;
               b = (int)floorf(tt);
               const float fr = tt - (float)b;
-              if (g.general || b < 0 || b >= nbins || fr < 1e-4f || fr > 1.f - 1e-4f) {
+              if (g.general || (unsigned)b >= (unsigned)nbins || fabsf(fr - 0.5f) > 0.5f - 1e-4f) {
                 // within float rounding of an edge (or edges not linear in r,
                 // where b is only a first guess): exact integer r^2 vs exact
                 // thresholds
