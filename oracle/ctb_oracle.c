@@ -184,6 +184,9 @@ int oracle_alm(const double* xyz, const double* w, int64_t n, double box, double
  *   wpairs [nbins]   sum_p w_p sum_{j in b} w_j      (NULL to skip)
  *   selfw  [nbins]   sum_p w_p sum_{j in b} w_j^2    (NULL to skip): the j = k
  *          part of each diagonal entry (P_l(1) = 1, times 4 pi/(2l+1) Y-sum)
+ *   wprim  [np] or NULL: the weight each listed primary carries in the sums
+ *          over p in place of w_p (its neighbours keep their own weights);
+ *          used for primaries that stand for a group of pivots
  *   npairs_out   number of binned (p, j) pairs
  *   namb_out     pairs whose separation lies within amb_tol (relative) of a
  *                bin edge, rmin or rmax: the ones a lower-precision binning
@@ -194,7 +197,8 @@ int oracle_alm(const double* xyz, const double* w, int64_t n, double box, double
 int oracle_zeta(const double* xyz, const double* w, int64_t n, double box, double rmin,
                 double rmax, int nbins, int lmax, const int64_t* prim, int64_t np,
                 double* zeta, double* gram, double* wpairs, double* selfw,
-                int64_t* npairs_out, int64_t* namb_out, double amb_tol, int nthreads)
+                int64_t* npairs_out, int64_t* namb_out, double amb_tol, int nthreads,
+                const double* wprim)
 {
     if (check_args(n, box, rmin, rmax, nbins, lmax)) return -1;
     if (!prim) np = n;
@@ -261,7 +265,7 @@ int oracle_zeta(const double* xyz, const double* w, int64_t n, double box, doubl
                 nb[b] += wj;
                 sb[b] += wj * wj;
             }
-            double wp = w ? w[p] : 1.0;
+            double wp = wprim ? wprim[i] : (w ? w[p] : 1.0);
             for (int b = 0; b < nbins; ++b) { pt[b] += wp * nb[b]; st[b] += wp * sb[b]; }
             for (int l = 0; l <= lmax; ++l) {
                 for (int b1 = 0; b1 < nbins; ++b1) {

@@ -64,11 +64,12 @@ static void tangent_frame(const double* n, double eE[3], double eN[3])
 /*
  * zeta [mmax+1][nbins][nbins], gram (same with |w_p|) and wpairs [nbins]
  * (sum_p w_p sum_{j in b} w_j) may be NULL except zeta.  prim: primaries (NULL
- * = all).  Returns 0, -1 on bad arguments, -2 on allocation failure.
+ * = all).  wprim [np] or NULL: the weight each listed primary carries in place
+ * of w_p (its neighbours keep their own).  Returns 0, -1 on bad arguments, -2 on allocation failure.
  */
 int oracle_zeta_sphere(const double* xyz, const double* w, int64_t n, double tmin, double tmax, int nbins,
                        int mmax, const int64_t* prim, int64_t np, double* zeta, double* gram, double* wpairs,
-                       int64_t* npairs_out, int nthreads)
+                       int64_t* npairs_out, int nthreads, const double* wprim)
 {
     if (n < 0 || nbins < 1 || mmax < 0 || mmax > SPHERE_MMAX_CAP || !(tmin >= 0.0) || !(tmax > tmin) ||
         tmax > 3.14159265358979323846)
@@ -136,7 +137,7 @@ int oracle_zeta_sphere(const double* xyz, const double* w, int64_t n, double tmi
                 }
                 nb[b] += wj;
             }
-            double wp = w ? w[p] : 1.0;
+            double wp = wprim ? wprim[i] : (w ? w[p] : 1.0);
             for (int b = 0; b < nbins; ++b) pt[b] += wp * nb[b];
             for (int m = 0; m <= mmax; ++m)
                 for (int b1 = 0; b1 < nbins; ++b1)

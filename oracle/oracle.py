@@ -50,9 +50,9 @@ def _load():
         lib.oracle_alm.argtypes = [vp, vp, i64, d, d, d, i32, i32, vp, i64, vp, vp, i32]
         lib.oracle_alm.restype = i32
         lib.oracle_zeta.argtypes = [vp, vp, i64, d, d, d, i32, i32, vp, i64,
-                                    vp, vp, vp, vp, vp, vp, d, i32]
+                                    vp, vp, vp, vp, vp, vp, d, i32, vp]
         lib.oracle_zeta.restype = i32
-        lib.oracle_zeta_sphere.argtypes = [vp, vp, i64, d, d, i32, i32, vp, i64, vp, vp, vp, vp, i32]
+        lib.oracle_zeta_sphere.argtypes = [vp, vp, i64, d, d, i32, i32, vp, i64, vp, vp, vp, vp, i32, vp]
         lib.oracle_zeta_sphere.restype = i32
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = i32
@@ -116,10 +116,20 @@ def alm(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, nthreads=0):
     return out
 
 
-def zeta(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, amb_tol=0.0, nthreads=0):
+def _wprim(wprim, np_):
+    if wprim is None:
+        return None
+    wprim = np.ascontiguousarray(wprim, dtype=np.float64)
+    if wprim.shape != (np_,):
+        raise ValueError("wprim needs one weight per primary")
+    return wprim
+
+
+def zeta(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, amb_tol=0.0, nthreads=0, wprim=None):
     """zeta_l(b1, b2) and its diagnostics, summed over the given primaries.
 
-    Returns a dict with ``zeta`` and ``gram`` ([lmax+1][nbins][nbins]),
+    ``wprim`` (one per primary, optional) replaces each primary's own weight
+    in the sum over primaries.  Returns a dict with ``zeta`` and ``gram`` ([lmax+1][nbins][nbins]),
     ``wpairs`` and ``selfw`` ([nbins]), ``npairs`` and ``namb`` (ints).
     """
     lib = _load()
@@ -127,6 +137,7 @@ def zeta(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, amb_tol=0.0, nthreads=
     prim = _prim(prim)
     n = xyz.shape[0]
     np_ = n if prim is None else prim.shape[0]
+    wprim = _wprim(wprim, np_)
     shape = (lmax + 1, nbins, nbins)
     z = np.zeros(shape)
     g = np.zeros(shape)
@@ -137,16 +148,17 @@ def zeta(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, amb_tol=0.0, nthreads=
     rc = lib.oracle_zeta(_ptr(xyz), _ptr(w), n, float(box), float(rmin), float(rmax),
                          int(nbins), int(lmax), _ptr(prim), np_, _ptr(z), _ptr(g),
                          _ptr(wp), _ptr(sw), ctypes.byref(npairs), ctypes.byref(namb),
-                         float(amb_tol), int(nthreads))
+                         float(amb_tol), int(nthreads), _ptr(wprim))
     if rc != 0:
         raise ValueError(f"oracle_zeta rejected its arguments (rc={rc})")
     return {"zeta": z, "gram": g, "wpairs": wp, "selfw": sw,
             "npairs": int(npairs.value), "namb": int(namb.value)}
 
 
-def zeta_sphere(xyz, w, theta_min, theta_max, nbins, mmax, prim=None, nthreads=0):
+def zeta_sphere(xyz, w, theta_min, theta_max, nbins, mmax, prim=None, nthreads=0, wprim=None):
     """Projected (angular) multipoles zeta_m(b1, b2) on the unit sphere, summed
-    over the given primaries (ctb_oracle_sphere.c states the definition).
+    over the given primaries (ctb_oracle_sphere.c states the definition);
+    ``wprim`` as in ``zeta``.
 
     Returns a dict with ``zeta`` and ``gram`` ([mmax+1][nbins][nbins]),
     ``wpairs`` ([nbins]) and ``npairs``.
@@ -156,6 +168,7 @@ def zeta_sphere(xyz, w, theta_min, theta_max, nbins, mmax, prim=None, nthreads=0
     prim = _prim(prim)
     n = xyz.shape[0]
     np_ = n if prim is None else prim.shape[0]
+    wprim = _wprim(wprim, np_)
     shape = (mmax + 1, nbins, nbins)
     z = np.zeros(shape)
     g = np.zeros(shape)
@@ -163,7 +176,7 @@ def zeta_sphere(xyz, w, theta_min, theta_max, nbins, mmax, prim=None, nthreads=0
     npairs = ctypes.c_int64(0)
     rc = lib.oracle_zeta_sphere(_ptr(xyz), _ptr(w), n, float(theta_min), float(theta_max), int(nbins),
                                 int(mmax), _ptr(prim), np_, _ptr(z), _ptr(g), _ptr(wp),
-                                ctypes.byref(npairs), int(nthreads))
+                                ctypes.byref(npairs), int(nthreads), _ptr(wprim))
     if rc != 0:
         raise ValueError(f"oracle_zeta_sphere rejected its arguments (rc={rc})")
     return {"zeta": z, "gram": g, "wpairs": wp, "npairs": int(npairs.value)}
