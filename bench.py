@@ -390,11 +390,12 @@ def run_ours(args):
 
     seq = batch and args.batch_mode == "sequential"
     seq_stats = {}
+    shared_h = args.shared if args.shared >= 0 and not batch and not args.primaries else None
 
     def step():
         if seq:
             # the same catalogues as plain launches, one set_points + compute each
-            tm, launches_, pairs_, chunks_ = np.zeros(8), 0, 0, 0
+            tm, launches_, pairs_, chunks_ = np.zeros(9), 0, 0, 0
             for i, (x, v) in enumerate(d_cats):
                 est.set_points(x, v)
                 est.compute(out=d_zeta[i])
@@ -408,7 +409,9 @@ def run_ours(args):
             est.compute_batch(d_cats, out=d_zeta)
             return
         est.set_points(d_xyz, d_w)
-        if d_prim is None:
+        if shared_h is not None:
+            est.compute_shared(shared_h, out=d_zeta)
+        elif d_prim is None:
             est.compute(out=d_zeta)
         else:
             est.compute_subset(d_prim, out=d_zeta)
@@ -417,6 +420,34 @@ def run_ours(args):
         flush.zero_()
         step()
     torch.cuda.synchronize(dev)
+
+    shared_info = None
+    if shared_h is not None:
+        # the exact estimator on the same catalogue, once, for the speed and the deviation
+        est.set_points(d_xyz, d_w)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        t0.record(stream)
+        z_exact = est.compute()
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        exact_ms, exact_pairs = t0.elapsed_time(t1), est.pair_count()
+        z_sh = est.compute_shared(shared_h)
+        h_used, n_groups_sh = est.pivot_groups()
+        if np.all(w > 0):
+            # positive weights: zeta itself is the Gram matrix of the tests' metric
+            diag = np.abs(np.einsum("lii->li", z_exact))
+            scale = np.sqrt(diag[:, :, None] * diag[:, None, :])
+            dev_metric = "max |zeta_shared - zeta_exact| / sqrt(zeta(b1,b1) zeta(b2,b2))"
+        else:
+            scale = np.broadcast_to(np.abs(z_exact).max(axis=(1, 2), keepdims=True), z_exact.shape)
+            dev_metric = "max over l of max |zeta_shared - zeta_exact| / max |zeta_exact|"
+        shared_info = {"pivot_cell": h_used, "groups": n_groups_sh, "points": int(xyz.shape[0]),
+                       "exact_pairs": exact_pairs, "exact_ms": exact_ms,
+                       "max_dev_vs_exact": float(np.max(np.abs(z_sh - z_exact) / np.where(scale > 0, scale, 1.0))),
+                       "dev_metric": dev_metric + ", against the exact path on the GPU"}
+        torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     pair_ms, launches, npairs, stages = [], 0, 0, []
@@ -463,7 +494,10 @@ def run_ours(args):
             est.compute_batch(list(zip(xyz, w)), out=zh)
         else:
             est.set_points(xyz, w)
-            est.compute(out=zh)
+            if shared_h is not None:
+                est.compute_shared(shared_h, out=zh)
+            else:
+                est.compute(out=zh)
         dt = time.perf_counter() - t0
         if k > 0:
             e2e_t.append(dt)
@@ -497,7 +531,8 @@ def run_ours(args):
                 "impl_flops_per_pair": flops_per_pair(kw["lmax"]), "impl_tflops": impl_tflops,
                 "impl_frac": impl_tflops / (2 * peak_tinst)}
     st = np.mean(np.array(stages), axis=0)
-    names = ["ingest", "sort_grid", "pair_total", "pack", "contraction", "reduce", "enumerate", "accumulate"]
+    names = ["ingest", "sort_grid", "pair_total", "pack", "contraction", "reduce", "enumerate", "accumulate",
+             "group"]
     stages_ms = {k: round(float(v), 3) for k, v in zip(names, st)}
     clocks = clk.summary()
     line = {
@@ -524,6 +559,10 @@ def run_ours(args):
         "wall_s": wall,
         "clocks": clocks,
     }
+    if shared_info is not None:
+        shared_info["speedup_vs_exact"] = shared_info["exact_ms"] / ms_per_step
+        line["config"]["estimator"] = "shared neighbour lists for close pivots (approximate)"
+        line["shared"] = shared_info
     if rank == 0 and not args.no_cpu_baseline:
         sx, sw = (xyz[0], w[0]) if batch else (xyz, w)
         rate, k, dt, _, ref = oracle_rate(sx, sw, kw, target_s=args.cpu_seconds, full=True)
@@ -559,6 +598,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-mode", default="batched", choices=["batched", "sequential"],
                     help="mock_batch: one ctb_compute_batch per step, or one set_points + compute per catalogue")
+    ap.add_argument("--shared", type=float, default=-1.0,
+                    help="time ctb_compute_shared (shared neighbour lists for close pivots) with this pivot "
+                         "cell side; 0 = the mean separation; negative = off (the exact estimator)")
     ap.add_argument("--cells-per-rmax", type=int, default=0,
                     help="grid cells per r_max (0: the library's autotuner picks)")
     args = ap.parse_args()

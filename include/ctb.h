@@ -162,6 +162,48 @@ int ctb_compute(ctb_ctx* ctx, double* zeta_out);
 int ctb_compute_subset(ctb_ctx* ctx, const int64_t* primary_idx, int64_t m, double* zeta_out);
 
 /*
+ * Shared neighbour lists for close pivots (paper, "Implementation": pivots
+ * close to one another share one neighbour list; the pivot radius is set
+ * from the mean separation unless the user gives one).  An approximation of
+ * ctb_compute that runs the pair pipeline once per group of pivots.
+ *   groups      a point belongs to the pivot cell (floor(x/h), floor(y/h),
+ *               floor(z/h)) of side h, cells aligned at the origin of
+ *               coordinates, taken on the coordinates as stored (periodic:
+ *               wrapped into [0, box) on the box / 2^32 grid; open: on a
+ *               power-of-two grid over the bounding box)
+ *   estimate    each group g is represented by its member of smallest
+ *               catalogue index c_g and carries W_g = sum of its members'
+ *               weights:
+ *                 zeta_l(b1,b2) ~= 4 pi/(2l+1) sum_g W_g sum_m a_lm(c_g,b1) a_lm(c_g,b2)
+ *               (on the sphere, zeta_m with the projected a_m), i.e. every
+ *               member takes its representative's neighbour list.
+ *   bound       per entry, |shared - ctb_compute| <= sum_p |w_p| [min(l (A1 S2
+ *               + S1 A2), 2 S1 S2) + D1 U2 + U1 D2], summed over non-
+ *               representatives p with representative c.  S_b and A_b are
+ *               the |w_j| sums, plain and times the angle between x_j - x_p
+ *               and x_j - x_c, over neighbours j in bin b from both p and c.
+ *               D_b and U_b are the |w_j| sums over j in b from exactly one
+ *               of them and from either.  The angular term follows from
+ *               Bernstein's inequality, |d/dgamma P_l(cos gamma)| <= l.  This
+ *               is a statement about the estimate, up to FP32 rounding of the
+ *               computation.
+ *   pivot_cell  h > 0, or 0 for the mean separation: (V / n)^(1/3) with
+ *               V = box^3 (periodic) or the product of the bounding box's
+ *               sides, each at least r_max (open); sqrt(4 pi / n) on the
+ *               sphere.
+ *   zeta_out    as ctb_compute.  ctb_get_2pcf then gives the same shared
+ *               estimate of the pair sums.
+ * Errors: as ctb_compute, plus CTB_ERR_ARG for h negative or not finite, or
+ * more than 2^64 pivot cells over the catalogue's extent.
+ */
+int ctb_compute_shared(ctb_ctx* ctx, double pivot_cell, double* zeta_out);
+
+/* The pivot cell side h and the number of groups of the last
+ * ctb_compute_shared.  CTB_ERR_STATE if there was none since the last
+ * ctb_set_points. */
+int ctb_get_pivot_groups(ctb_ctx* ctx, double* pivot_cell, int64_t* groups);
+
+/*
  * Export a_lm(p, b) of the listed primaries (debug / parity; the same
  * coefficients the contraction consumes, rounded to float32).
  *   primary_idx  [m] int64 catalogue indices, host or device
@@ -226,7 +268,8 @@ int ctb_set_allocator(ctb_ctx* ctx, void* (*alloc)(size_t bytes, void* user),
  *   [0] ingest  [1] sort + grid  [2] pair multipoles (= [6] + [7])  [3] pack
  *   [4] contraction  [5] reduce + normalise
  *   [6] neighbour enumeration (count + scan + fill)  [7] harmonic accumulation
- * Writes min(cap, 8) values; returns the number written.
+ *   [8] pivot grouping (ctb_compute_shared; 0 otherwise)
+ * Writes min(cap, 9) values; returns the number written.
  */
 int ctb_get_timings(ctb_ctx* ctx, double* ms_per_stage, int cap);
 

@@ -23,7 +23,7 @@ struct Buf {
 
 thread_local std::string g_create_err;
 
-constexpr int kStages = 8;
+constexpr int kStages = 9;
 
 }  // namespace
 
@@ -54,6 +54,7 @@ struct ctb_ctx {
   Geom g{};
   double unit = 0;
   double origin[3] = {0, 0, 0};
+  double hi[3] = {0, 0, 0};  // largest coordinate per axis (box for a periodic box)
   double bbox_volume = 0;
   Layout lay{};
   int Lk = 0;
@@ -67,13 +68,18 @@ struct ctb_ctx {
   int pairsum_segs = 0;  // catalogues they cover (0: none)
   int pairsum_parts = 0;
   Buf codes, code_base;  // per-candidate bin codes of a chunk; range start per (primary, row block)
+  // shared neighbour lists: sort buffers, segment heads, group ids, scan scratch, representatives, weights
+  Buf gk0, gv0, gk1, gv1, glo, ghi, ghead, gid, gscan, gprim, gw;
+  const float* wsub = nullptr;  // primary weights replacing the points' own during a shared compute
+  double shared_h = 0;          // pivot cell side of the last ctb_compute_shared
+  int64_t ngroups = -1;         // its groups (-1: none since ctb_set_points)
   Buf counts, offsets, scan_tmp2;
   Buf ops[4], slot_lm, lbase_d, kp_d, partial_tc, conv_off, conv_src, conv_coef;
   uint64_t list_cap = (uint64_t)1 << 32;  // neighbour-list entries per chunk (16 GB)
   const uint32_t* batch_keys = nullptr;    // sorted keys while a batch is loaded
   cudaEvent_t ev[16] = {};
   bool ev_ready = false;
-  double t_ms[kStages] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double t_ms[kStages] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t npairs = 0;
   uint64_t nchunks = 0;  // primary chunks of the last compute
   unsigned long long launches_points = 0, launches_compute = 0;
@@ -150,7 +156,8 @@ void release_all(ctb_ctx* c) {
                 &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr, &c->codes, &c->code_base, &c->pairsum, &c->edge_in, &c->edge_tj, &c->counts,
                 &c->offsets, &c->scan_tmp2, &c->ops[0], &c->ops[1], &c->ops[2], &c->ops[3],
                 &c->slot_lm, &c->lbase_d, &c->kp_d, &c->partial_tc, &c->conv_off, &c->conv_src,
-                &c->conv_coef};
+                &c->conv_coef, &c->gk0, &c->gv0, &c->gk1, &c->gv1, &c->glo, &c->ghi, &c->ghead, &c->gid, &c->gscan,
+                &c->gprim, &c->gw};
   for (Buf* b : all) release(c, *b);
   c->tables_ready = false;
 }
@@ -382,6 +389,8 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
   c->n = -1;
   c->batch_keys = nullptr;
   c->pairsum_segs = 0;
+  c->ngroups = -1;
+  c->shared_h = 0;
   const double* dxyz = xyz;
   const double* dw = w;
   if (n > 0 && !is_device_ptr(xyz)) {
@@ -411,6 +420,7 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
     double ncd = std::floor(c->box * cpr / c->rmax);
     nc = (uint32_t)std::max(1.0, std::min(ncd, 1024.0));
     c->origin[0] = c->origin[1] = c->origin[2] = 0;
+    c->hi[0] = c->hi[1] = c->hi[2] = c->box;
   } else {
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     if (n > 0) {
@@ -446,7 +456,10 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
     // dyadic grid is represented exactly
     c->unit = std::ldexp(1.0, (int)std::ceil(std::log2(ext / (2147483648.0 - 1024.0))));
     while (ext / c->unit > 2147483648.0 - 1024.0) c->unit *= 2.0;
-    for (int k = 0; k < 3; ++k) c->origin[k] = lo[k];
+    for (int k = 0; k < 3; ++k) {
+      c->origin[k] = lo[k];
+      c->hi[k] = hi[k];
+    }
     g.shift = 31;
     double rmax_u = c->rmax / c->unit;
     double ncd = std::ceil(2147483648.0 * cpr / rmax_u);
@@ -652,6 +665,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   sa.counts = P<uint32_t>(c->counts);
   sa.offsets = P<uint32_t>(c->offsets);
   sa.wprim = P<float>(c->wprim);
+  sa.wsub = c->wsub;
   sa.work = work;
   sa.total = total;
   sa.keys = c->batch_keys;
@@ -1020,6 +1034,102 @@ int map_primaries(ctb_ctx* c, const int64_t* idx, int64_t m) {
   return CTB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// shared neighbour lists: group the points by pivot cell, then run the pair
+// pipeline over the groups' representatives with the group weights
+
+// key bits a radix sort needs for keys below ncells (<= 2^64, as a double)
+int key_bits(double ncells) {
+  int b = 0;
+  while (b < 64 && std::ldexp(1.0, b) < ncells) ++b;
+  return b;
+}
+
+int shared_impl(ctb_ctx* c, double h, double* zeta_out) {
+  if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
+  if (!zeta_out) return fail(c, CTB_ERR_ARG, "zeta_out is NULL");
+  if (!std::isfinite(h) || h < 0) return fail(c, CTB_ERR_ARG, "pivot cell side must be >= 0 and finite");
+  const int64_t n = c->n;
+  if (h == 0 && n > 0) {
+    // the mean separation of the catalogue
+    if (c->sphere) {
+      h = std::sqrt(4.0 * M_PI / (double)n);
+    } else {
+      const double vol = c->periodic ? c->box * c->box * c->box : c->bbox_volume;
+      h = std::cbrt(vol / (double)n);
+    }
+  }
+  CK(c, cudaSetDevice(c->dev));
+  int64_t ng = 0;
+  double t_group = 0;
+  if (n > 0) {
+    PivotGrid pg{};
+    pg.unit = c->unit;
+    pg.h = h;
+    double ncell = 1.0;
+    for (int k = 0; k < 3; ++k) {
+      pg.origin[k] = c->origin[k];
+      const double k0 = std::floor(c->origin[k] / h), k1 = std::floor(c->hi[k] / h);
+      ncell *= k1 - k0 + 1.0;
+      // cell indices stay well inside int64, each axis inside uint32, the product inside uint64
+      if (!(std::fabs(k0) < 0x1p62 && std::fabs(k1) < 0x1p62 && k1 - k0 + 1.0 < 4294967296.0 &&
+            ncell <= 18446744073709551616.0))
+        return fail(c, CTB_ERR_ARG, "pivot cells: more than 2^64 over the catalogue's extent");
+      pg.k0[k] = (long long)k0;
+      pg.n[k] = (uint32_t)(k1 - k0 + 1.0);
+    }
+    const size_t nn = (size_t)n;
+    CK(c, ensure(c, c->gk0, nn * 4));
+    CK(c, ensure(c, c->gv0, nn * 4));
+    CK(c, ensure(c, c->gk1, nn * 4));
+    CK(c, ensure(c, c->gv1, nn * 4));
+    CK(c, ensure(c, c->glo, nn * 4));
+    CK(c, ensure(c, c->ghi, nn * 4));
+    CK(c, ensure(c, c->ghead, nn * 4));
+    CK(c, ensure(c, c->gid, nn * 4));
+    CK(c, ensure(c, c->gscan, scan_tmp_words(nn) * 4));
+    CK(c, ensure(c, c->gprim, nn * 4));
+    CK(c, ensure(c, c->gw, nn * 4));
+    CK(c, cudaEventRecord(c->ev[12], c->st));
+    CK(c, launch_pivot_key(P<uint4>(c->pts), P<uint32_t>(c->i2s), n, pg, P<uint32_t>(c->glo), P<uint32_t>(c->ghi),
+                           P<uint32_t>(c->gk0), P<uint32_t>(c->gv0), c->st));
+    // stable LSD sort: low 32 key bits, then the high ones
+    const int bits = key_bits(ncell);
+    SortBufs sb{P<uint32_t>(c->gk0), P<uint32_t>(c->gv0), P<uint32_t>(c->gk1), P<uint32_t>(c->gv1),
+                P<uint32_t>(c->hist), P<uint32_t>(c->scan_tmp)};
+    bool in1 = false;
+    CK(c, radix_sort(sb, n, std::min(bits, 32), &in1, c->st));
+    const uint32_t* vs = in1 ? sb.v1 : sb.v0;
+    if (bits > 32) {
+      SortBufs hb{in1 ? sb.k0 : sb.k1, in1 ? sb.v1 : sb.v0, in1 ? sb.k1 : sb.k0, in1 ? sb.v0 : sb.v1, sb.hist,
+                  sb.scan_tmp};
+      CK(c, launch_gather_hi(hb.v0, P<uint32_t>(c->ghi), n, hb.k0, c->st));
+      bool hin1 = false;
+      CK(c, radix_sort(hb, n, bits - 32, &hin1, c->st));
+      vs = hin1 ? hb.v1 : hb.v0;
+    }
+    CK(c, launch_group_heads(vs, P<uint32_t>(c->glo), P<uint32_t>(c->ghi), n, P<uint32_t>(c->ghead), c->st));
+    CK(c, exclusive_scan_u32(P<uint32_t>(c->ghead), P<uint32_t>(c->gid), nn, P<uint32_t>(c->gscan), c->st));
+    CK(c, launch_group_reduce(vs, P<uint32_t>(c->ghead), P<uint32_t>(c->gid), n, P<uint4>(c->pts),
+                              P<uint32_t>(c->i2s), P<uint32_t>(c->gprim), P<float>(c->gw), c->st));
+    CK(c, cudaEventRecord(c->ev[13], c->st));
+    uint32_t last[2] = {0, 0};
+    CK(c, cudaMemcpyAsync(&last[0], P<uint32_t>(c->gid) + (n - 1), 4, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(&last[1], P<uint32_t>(c->ghead) + (n - 1), 4, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    ng = (int64_t)last[0] + (int64_t)last[1];
+    t_group = elapsed(c->ev[12], c->ev[13]);
+  }
+  c->wsub = P<float>(c->gw);
+  const int r = compute_impl(c, P<uint32_t>(c->gprim), ng, zeta_out);
+  c->wsub = nullptr;
+  if (r) return r;
+  c->t_ms[8] = t_group;
+  c->shared_h = h;
+  c->ngroups = ng;
+  return CTB_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1185,6 +1295,22 @@ int ctb_compute_subset(ctb_ctx* c, const int64_t* primary_idx, int64_t m, double
   int r = map_primaries(c, primary_idx, m);
   if (r) return r;
   return compute_impl(c, m > 0 ? P<uint32_t>(c->prim) : nullptr, m, zeta_out);
+}
+
+int ctb_compute_shared(ctb_ctx* c, double pivot_cell, double* zeta_out) {
+  if (!c) return CTB_ERR_ARG;
+  const unsigned long long l0 = g_launches;
+  int r = shared_impl(c, pivot_cell, zeta_out);
+  c->launches_compute = g_launches - l0;
+  return r;
+}
+
+int ctb_get_pivot_groups(ctb_ctx* c, double* pivot_cell, int64_t* groups) {
+  if (!c || !pivot_cell || !groups) return CTB_ERR_ARG;
+  if (c->ngroups < 0) return fail(c, CTB_ERR_STATE, "no ctb_compute_shared since the last ctb_set_points");
+  *pivot_cell = c->shared_h;
+  *groups = c->ngroups;
+  return CTB_OK;
 }
 
 int ctb_get_alm(ctb_ctx* c, const int64_t* primary_idx, int64_t m, float* alm_out) {

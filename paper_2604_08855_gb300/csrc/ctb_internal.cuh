@@ -196,6 +196,27 @@ cudaError_t launch_gather(const uint32_t* val_sorted, const uint4* pts_in, int64
 cudaError_t launch_cell_start(const uint32_t* key_sorted, int64_t n, uint32_t ncells, uint32_t* cell_start,
                               uint32_t* scan_tmp, cudaStream_t st);
 
+// shared.cu -- pivot groups for shared neighbour lists
+struct PivotGrid {
+  double origin[3];  // stored coordinate = origin + u * unit
+  double unit;
+  double h;          // pivot cell side
+  long long k0[3];   // floor(lo / h) per axis: the first cell
+  uint32_t n[3];     // cells per axis (product <= 2^64)
+};
+// key_lo / key_hi: the 64-bit cell key of each point (catalogue order);
+// sort_key: a copy of key_lo for the sort; val: the catalogue index
+cudaError_t launch_pivot_key(const uint4* pts, const uint32_t* i2s, int64_t n, const PivotGrid& pg,
+                             uint32_t* key_lo, uint32_t* key_hi, uint32_t* sort_key, uint32_t* val,
+                             cudaStream_t st);
+cudaError_t launch_gather_hi(const uint32_t* val, const uint32_t* key_hi, int64_t n, uint32_t* out,
+                             cudaStream_t st);
+cudaError_t launch_group_heads(const uint32_t* val_sorted, const uint32_t* key_lo, const uint32_t* key_hi,
+                               int64_t n, uint32_t* head, cudaStream_t st);
+cudaError_t launch_group_reduce(const uint32_t* val_sorted, const uint32_t* head, const uint32_t* gid, int64_t n,
+                                const uint4* pts, const uint32_t* i2s, uint32_t* prim_out, float* w_out,
+                                cudaStream_t st);
+
 // stream.cu -- neighbour enumeration (count pass, then fill pass)
 struct StreamArgs {
   const uint4* pts;               // sorted points
@@ -208,6 +229,7 @@ struct StreamArgs {
   const uint32_t* offsets;        // [prim_count][nbins] list start per (primary, bin) (fill pass)
   uint32_t* lists;                // neighbour indices grouped by (primary, bin)      (fill pass)
   float* wprim;                   // [prim_count] primary weights                      (count pass)
+  const float* wsub;              // weights replacing the primaries' own, indexed like prim (NULL: none)
   unsigned long long* work;       // work counter (zeroed before launch)
   unsigned long long* total;      // binned pairs of this launch (count pass, accumulated)
   const uint32_t* keys;           // sorted cell keys of a batch (catalogue = key / ncells), or NULL

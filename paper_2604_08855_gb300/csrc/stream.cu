@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
     const uint4 P = __ldg(a.pts + sp);
     // batch: the primary's catalogue owns cells [cat * ncells, (cat + 1) * ncells)
     rw.cbase = a.keys ? (__ldg(a.keys + sp) / g.ncells) * g.ncells : 0u;
-    if (!FILL && lane == 0) a.wprim[i] = __uint_as_float(P.w);
+    if (!FILL && lane == 0) a.wprim[i] = a.wsub ? __ldg(a.wsub + gi) : __uint_as_float(P.w);
     const uint64_t ib = i * (uint64_t)nbins;
     if (FILL) {
       for (int b = lane; b < nbins; b += 32) cnt[b] = __ldg(a.offsets + ib + b);

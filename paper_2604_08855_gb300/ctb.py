@@ -29,7 +29,8 @@ PREC_FP32, PREC_BF16X3, PREC_TF32 = 0, 1, 2
 LMAX_CAP, NBINS_CAP, MMAX_CAP = 20, 64, 16
 
 # every symbol include/ctb.h declares
-EXPORTS = ("ctb_create", "ctb_create_sphere", "ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm",
+EXPORTS = ("ctb_create", "ctb_create_sphere", "ctb_set_points", "ctb_compute", "ctb_compute_subset",
+           "ctb_compute_shared", "ctb_get_pivot_groups", "ctb_get_alm",
            "ctb_compute_batch", "ctb_set_option", "ctb_set_stream", "ctb_set_allocator",
            "ctb_get_timings", "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_grid",
            "ctb_get_2pcf", "ctb_edge_correct", "ctb_get_launch_count", "ctb_contract_noalloc", "ctb_destroy", "ctb_last_error", "ctb_version")
@@ -61,6 +62,8 @@ def load(path: str | None = None):
     lib.ctb_compute.argtypes = [vp, vp]
     lib.ctb_compute_subset.argtypes = [vp, vp, i64, vp]
     lib.ctb_get_alm.argtypes = [vp, vp, i64, vp]
+    lib.ctb_compute_shared.argtypes = [vp, d, vp]
+    lib.ctb_get_pivot_groups.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
     lib.ctb_compute_batch.argtypes = [vp, vp, vp, vp, i32, vp]
     lib.ctb_set_option.argtypes = [vp, i32, i64]
     lib.ctb_set_stream.argtypes = [vp, vp]
@@ -79,7 +82,8 @@ def load(path: str | None = None):
     lib.ctb_last_error.restype = ctypes.c_char_p
     lib.ctb_version.argtypes = []
     lib.ctb_version.restype = ctypes.c_char_p
-    for name in ("ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_get_alm", "ctb_compute_batch",
+    for name in ("ctb_set_points", "ctb_compute", "ctb_compute_subset", "ctb_compute_shared",
+                 "ctb_get_pivot_groups", "ctb_get_alm", "ctb_compute_batch",
                  "ctb_set_option", "ctb_set_stream", "ctb_set_allocator", "ctb_get_timings",
                  "ctb_get_pair_count", "ctb_get_chunk_count", "ctb_get_grid", "ctb_get_2pcf",
                  "ctb_edge_correct", "ctb_get_launch_count", "ctb_contract_noalloc"):
@@ -223,6 +227,22 @@ class CTB:
         self._check(self.lib.ctb_compute_subset(self._h, _ptr(p), int(p.shape[0]), _ptr(z)))
         return z
 
+    def compute_shared(self, pivot_cell=0.0, out=None):
+        """Shared neighbour lists for close pivots: the approximation of zeta in
+        which every point takes the neighbour list of its pivot cell's
+        representative (include/ctb.h states it and its error bound).
+        pivot_cell: the cell side h, 0 for the mean separation."""
+        z = self._out(out, self.zeta_shape, np.float64)
+        self._check(self.lib.ctb_compute_shared(self._h, float(pivot_cell), _ptr(z)))
+        return z
+
+    def pivot_groups(self):
+        """(h, groups) of the last compute_shared."""
+        h = ctypes.c_double(0.0)
+        g = ctypes.c_int64(0)
+        self._check(self.lib.ctb_get_pivot_groups(self._h, ctypes.byref(h), ctypes.byref(g)))
+        return float(h.value), int(g.value)
+
     def get_alm(self, primaries, out=None):
         p = primaries if hasattr(primaries, "data_ptr") else np.ascontiguousarray(primaries, dtype=np.int64)
         a = self._out(out, (int(p.shape[0]), self.nbins, self.ncoef), np.float32)
@@ -243,9 +263,10 @@ class CTB:
         return z
 
     def timings(self):
-        """ms per stage: ingest, sort+grid, pair, pack, contraction, reduce, enumeration, accumulation."""
-        buf = (ctypes.c_double * 8)()
-        k = self._check(self.lib.ctb_get_timings(self._h, ctypes.cast(buf, ctypes.c_void_p), 8))
+        """ms per stage: ingest, sort+grid, pair, pack, contraction, reduce, enumeration, accumulation,
+        pivot grouping."""
+        buf = (ctypes.c_double * 9)()
+        k = self._check(self.lib.ctb_get_timings(self._h, ctypes.cast(buf, ctypes.c_void_p), 9))
         return list(buf)[:k]
 
     def launch_count(self) -> int:
