@@ -610,17 +610,18 @@ int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, siz
     size_t elems = 0;
     tc_layout(tf32, cnt, nb, c->lmax, lb, kp, &elems);
     const size_t esz = tf32 ? 4 : 2;
+    // the pack kernel writes every element, the K padding of each (l, bin) included
     for (int k = 0; k < 4; ++k) {
       if (tf32 && (k == 1 || k == 3)) continue;
       CK(c, ensure(c, c->ops[k], elems * esz));
-      CK(c, cudaMemsetAsync(c->ops[k].p, 0, elems * esz, c->st));
     }
     CK(c, ensure(c, c->lbase_d, lb.size() * 8));
     CK(c, ensure(c, c->kp_d, kp.size() * 8));
     CK(c, cudaMemcpyAsync(c->lbase_d.p, lb.data(), lb.size() * 8, cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemcpyAsync(c->kp_d.p, kp.data(), kp.size() * 8, cudaMemcpyHostToDevice, c->st));
     CK(c, launch_pack(tf32, M, wp, cnt, nb, c->lay.row, c->lmax, P<int>(c->slot), P<unsigned long long>(c->lbase_d),
-                      P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p, c->ops[2].p, c->ops[3].p, c->st));
+                      P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p, c->ops[2].p, c->ops[3].p,
+                      P<unsigned int>(c->flags) + 1, c->st));
     CK(c, cudaEventRecord(*ev_pack, c->st));
     CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), c->ops[0].p, c->ops[1].p, c->ops[2].p,
                              c->ops[3].p, P<double>(c->partial_tc) + seg * pl.ncon * zsz, pl.ncon,

@@ -330,13 +330,87 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
 // ---------------------------------------------------------------------------
 // pack: coefficient rows -> K-major operands per l
 
-// A block takes kPackPrims consecutive primaries.  For each bin it stages
-// their rows in shared memory (coalesced row reads), then writes, for each l,
-// the operands of those primaries: a contiguous span of kPackPrims * (2l+1)
-// elements of the (l, bin) region, in coalesced stores.  A = w_p a and B = a,
-// each as a BF16 hi + lo pair (or rounded to TF32).
+// A block takes kPackPrims consecutive primaries.  For each bin, one thread
+// copies their rows (contiguous, row * 4 bytes each) into shared memory with
+// TMA bulk copies completing on an mbarrier, two bins ahead in a two-stage
+// ring, so the copies of the next bin overlap the conversion of this one.
+// For each l the block's operands of one bin are a contiguous span of
+// kPackPrims * (2l+1) elements starting at a multiple of 16 elements; span l
+// starts at 16 l^2 of the bin's concatenated spans.  Each thread converts
+// chunks of 8 consecutive elements (chunk k lies in span l = floor(sqrt(k/2)))
+// and writes them with 16-byte stores.  A = w_p a and B = a, each as a BF16
+// hi + lo pair (or rounded to TF32).  A partial last block converts element
+// by element; block 0 also writes the zeros of the K padding.
 constexpr int kPackPrims = 16;
 constexpr int kPackThreads = 256;
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);  // .x = lo_elem (lower address)
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void pack_store(void* outA_hi, void* outA_lo, void* outB_hi, void* outB_lo,
+                                           unsigned long long idx, const float* av, const float* v) {
+  if constexpr (TF32) {
+    uint32_t ta[8], tb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta[i]) : "f"(av[i]));
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb[i]) : "f"(v[i]));
+    }
+    uint4* A = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(outA_hi) + idx);
+    uint4* B = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(outB_hi) + idx);
+    A[0] = make_uint4(ta[0], ta[1], ta[2], ta[3]);
+    A[1] = make_uint4(ta[4], ta[5], ta[6], ta[7]);
+    B[0] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
+    B[1] = make_uint4(tb[4], tb[5], tb[6], tb[7]);
+  } else {
+    float ah[8], al[8], bh[8], bl[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      ah[i] = __bfloat162float(__float2bfloat16_rn(av[i]));
+      al[i] = av[i] - ah[i];
+      bh[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
+      bl[i] = v[i] - bh[i];
+    }
+    const unsigned long long o = idx / 8;  // 8 BF16 = 16 bytes
+    reinterpret_cast<uint4*>(outA_hi)[o] = make_uint4(pack_bf16x2(ah[0], ah[1]), pack_bf16x2(ah[2], ah[3]),
+                                                      pack_bf16x2(ah[4], ah[5]), pack_bf16x2(ah[6], ah[7]));
+    reinterpret_cast<uint4*>(outA_lo)[o] = make_uint4(pack_bf16x2(al[0], al[1]), pack_bf16x2(al[2], al[3]),
+                                                      pack_bf16x2(al[4], al[5]), pack_bf16x2(al[6], al[7]));
+    reinterpret_cast<uint4*>(outB_hi)[o] = make_uint4(pack_bf16x2(bh[0], bh[1]), pack_bf16x2(bh[2], bh[3]),
+                                                      pack_bf16x2(bh[4], bh[5]), pack_bf16x2(bh[6], bh[7]));
+    reinterpret_cast<uint4*>(outB_lo)[o] = make_uint4(pack_bf16x2(bl[0], bl[1]), pack_bf16x2(bl[2], bl[3]),
+                                                      pack_bf16x2(bl[4], bl[5]), pack_bf16x2(bl[6], bl[7]));
+  }
+}
+
+template <bool TF32>
+__device__ __forceinline__ void pack_store1(void* outA_hi, void* outA_lo, void* outB_hi, void* outB_lo,
+                                            unsigned long long idx, float av, float v) {
+  if constexpr (TF32) {
+    uint32_t ta, tb;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta) : "f"(av));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb) : "f"(v));
+    reinterpret_cast<uint32_t*>(outA_hi)[idx] = ta;
+    reinterpret_cast<uint32_t*>(outB_hi)[idx] = tb;
+  } else {
+    const __nv_bfloat16 ah = __float2bfloat16_rn(av);
+    const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+    reinterpret_cast<__nv_bfloat16*>(outA_hi)[idx] = ah;
+    reinterpret_cast<__nv_bfloat16*>(outA_lo)[idx] = __float2bfloat16_rn(av - __bfloat162float(ah));
+    reinterpret_cast<__nv_bfloat16*>(outB_hi)[idx] = bh;
+    reinterpret_cast<__nv_bfloat16*>(outB_lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(bh));
+  }
+}
 
 template <bool TF32>
 __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__ M, const float* __restrict__ wprim,
@@ -345,52 +419,108 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
                                                        const unsigned long long* __restrict__ lbase,
                                                        const unsigned long long* __restrict__ kp,
                                                        void* __restrict__ outA_hi, void* __restrict__ outA_lo,
-                                                       void* __restrict__ outB_hi, void* __restrict__ outB_lo) {
-  extern __shared__ float s_pack[];
-  float* rows = s_pack;                          // [kPackPrims][row]
-  float* s_w = rows + kPackPrims * row;          // [kPackPrims]
+                                                       void* __restrict__ outB_hi, void* __restrict__ outB_lo,
+                                                       unsigned int* err, long long timeout_cycles) {
+  extern __shared__ __align__(16) float s_pack[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_abort;
+  __shared__ unsigned long long s_lbase[kLmaxCap + 1], s_kp[kLmaxCap + 1];
+  float* stage0 = s_pack;                                  // [kPackPrims][row], two stages
+  float* s_w = stage0 + 2 * kPackPrims * row;              // [kPackPrims]
   int* s_slot = reinterpret_cast<int*>(s_w + kPackPrims);  // [(lmax+1)^2]
   const int nc = (lmax + 1) * (lmax + 1);
   const int64_t p0 = (int64_t)blockIdx.x * kPackPrims;
   const int pt = (int)min((int64_t)kPackPrims, np - p0);
+  const uint32_t rowbytes = (uint32_t)row * 4u;
   for (int c = threadIdx.x; c < nc; c += blockDim.x) s_slot[c] = slot[c];
   for (int q = threadIdx.x; q < pt; q += blockDim.x) s_w[q] = __ldg(wprim + p0 + q);
-  for (int b = 0; b < nbins; ++b) {
-    __syncthreads();  // the previous bin's rows are consumed (and the tables on entry)
-    for (int q = 0; q < pt; ++q) {
-      const float* src = M + ((p0 + q) * nbins + b) * (int64_t)row;
-      for (int c = threadIdx.x; c < row; c += blockDim.x) rows[q * row + c] = __ldcs(src + c);
-    }
-    __syncthreads();
+  for (int l = threadIdx.x; l <= lmax; l += blockDim.x) {
+    s_lbase[l] = lbase[l];
+    s_kp[l] = kp[l];
+  }
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // stage s holds bin b (s = b & 1); its copies complete phase (b >> 1) of s_bar[s]
+  auto issue = [&](int b) {
+    float* dst = stage0 + (b & 1) * kPackPrims * row;
+    uint64_t* bar = &s_bar[b & 1];
+    mbar_expect_tx(bar, rowbytes * (uint32_t)pt);
+    for (int q = 0; q < pt; ++q) bulk_g2s(dst + q * row, M + ((p0 + q) * nbins + b) * (int64_t)row, rowbytes, bar);
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (nbins > 1) issue(1);
+  }
+  if (blockIdx.x == 0) {
+    // zeros in the K padding of every (l, bin): elements [np (2l+1), kp[l]) of its region
     for (int l = 0; l <= lmax; ++l) {
-      const int nl = 2 * l + 1;
-      const float inv = 1.f / (float)nl;
-      const unsigned long long base = lbase[l] + (unsigned long long)b * kp[l] + (unsigned long long)p0 * nl;
-      const int count = pt * nl;
-      for (int e = threadIdx.x; e < count; e += blockDim.x) {
-        const int q = (int)(((float)e + 0.5f) * inv);  // e / nl, exact for these sizes
-        const int mi = e - q * nl;
-        const float v = rows[q * row + s_slot[l * l + mi]];
-        const float av = s_w[q] * v;
-        const unsigned long long idx = base + (unsigned long long)e;
-        if (TF32) {
-          uint32_t ta, tb;
-          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta) : "f"(av));
-          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb) : "f"(v));
-          reinterpret_cast<uint32_t*>(outA_hi)[idx] = ta;
-          reinterpret_cast<uint32_t*>(outB_hi)[idx] = tb;
-        } else {
-          const __nv_bfloat16 ah = __float2bfloat16_rn(av);
-          const __nv_bfloat16 al = __float2bfloat16_rn(av - __bfloat162float(ah));
-          const __nv_bfloat16 bh = __float2bfloat16_rn(v);
-          const __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(bh));
-          reinterpret_cast<__nv_bfloat16*>(outA_hi)[idx] = ah;
-          reinterpret_cast<__nv_bfloat16*>(outA_lo)[idx] = al;
-          reinterpret_cast<__nv_bfloat16*>(outB_hi)[idx] = bh;
-          reinterpret_cast<__nv_bfloat16*>(outB_lo)[idx] = bl;
+      const unsigned long long used = (unsigned long long)np * (2 * l + 1);
+      const int tail = (int)(s_kp[l] - used);
+      for (int e = threadIdx.x; e < nbins * tail; e += blockDim.x) {
+        const int bb = e / tail, t = e - bb * tail;
+        pack_store1<TF32>(outA_hi, outA_lo, outB_hi, outB_lo,
+                          s_lbase[l] + (unsigned long long)bb * s_kp[l] + used + (unsigned long long)t, 0.f, 0.f);
+      }
+    }
+  }
+  int b = 0;
+  for (; b < nbins; ++b) {
+    mbar_wait(&s_bar[b & 1], (uint32_t)(b >> 1) & 1u, &s_abort, err, timeout_cycles);
+    __syncthreads();
+    if (s_abort) break;
+    const float* rows = stage0 + (b & 1) * kPackPrims * row;
+    if (pt == kPackPrims) {
+      const int nchunks = 2 * nc;  // 16 (l+1)^2 elements per bin, 8 per chunk
+      for (int k = threadIdx.x; k < nchunks; k += blockDim.x) {
+        const int t = k >> 1;
+        int l = (int)sqrtf((float)t);
+        while ((l + 1) * (l + 1) <= t) ++l;
+        while (l * l > t) --l;
+        const int nl = 2 * l + 1;
+        const int e0 = 8 * k - 16 * l * l;  // first element of the chunk in span l
+        int q = e0 / nl;
+        int mi = e0 - q * nl;
+        float v[8], av[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          v[i] = rows[q * row + s_slot[l * l + mi]];
+          av[i] = s_w[q] * v[i];
+          if (++mi == nl) {
+            mi = 0;
+            ++q;
+          }
+        }
+        const unsigned long long idx = s_lbase[l] + (unsigned long long)b * s_kp[l] +
+                                       (unsigned long long)p0 * nl + (unsigned long long)e0;
+        pack_store<TF32>(outA_hi, outA_lo, outB_hi, outB_lo, idx, av, v);
+      }
+    } else {
+      for (int l = 0; l <= lmax; ++l) {
+        const int nl = 2 * l + 1;
+        const unsigned long long base = s_lbase[l] + (unsigned long long)b * s_kp[l] + (unsigned long long)p0 * nl;
+        for (int e = threadIdx.x; e < pt * nl; e += blockDim.x) {
+          const int q = e / nl, mi = e - q * nl;
+          const float v = rows[q * row + s_slot[l * l + mi]];
+          pack_store1<TF32>(outA_hi, outA_lo, outB_hi, outB_lo, base + (unsigned long long)e, s_w[q] * v, v);
         }
       }
     }
+    __syncthreads();  // stage (b & 1) is consumed
+    if (threadIdx.x == 0 && b + 2 < nbins) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(b + 2);
+    }
+  }
+  if (s_abort && threadIdx.x == 0) {
+    // bounded wait for this block's own copies still in flight: bins b .. min(b + 1, nbins - 1)
+    int dummy = 0;
+    for (int c = b; c < nbins && c < b + 2; ++c)
+      mbar_wait(&s_bar[c & 1], (uint32_t)(c >> 1) & 1u, &dummy, err, timeout_cycles);
   }
 }
 
@@ -449,21 +579,21 @@ void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned 
 
 cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row, int lmax,
                         const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* ahi,
-                        void* alo, void* bhi, void* blo, cudaStream_t st) {
+                        void* alo, void* bhi, void* blo, unsigned int* err, cudaStream_t st) {
   if (np == 0) return cudaSuccess;
   const int64_t blocks = (np + kPackPrims - 1) / kPackPrims;
-  const size_t smem = ((size_t)kPackPrims * row + kPackPrims + (size_t)(lmax + 1) * (lmax + 1)) * 4;
+  const size_t smem = ((size_t)2 * kPackPrims * row + kPackPrims + (size_t)(lmax + 1) * (lmax + 1)) * 4;
   cudaError_t e;
   if (tf32) {
     e = cudaFuncSetAttribute(k_pack<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_pack<true><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, ahi,
-                                                               alo, bhi, blo);
+                                                               alo, bhi, blo, err, kTcTimeoutCycles);
   } else {
     e = cudaFuncSetAttribute(k_pack<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_pack<false><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, ahi,
-                                                                alo, bhi, blo);
+                                                                alo, bhi, blo, err, kTcTimeoutCycles);
   }
   ++g_launches;
   return cudaGetLastError();

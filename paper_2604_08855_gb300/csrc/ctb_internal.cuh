@@ -302,7 +302,7 @@ void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned 
 // slot: the layout's slot of coefficient l*l+l+m (l <= lmax)
 cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row, int lmax,
                         const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* ahi,
-                        void* alo, void* bhi, void* blo, cudaStream_t st);
+                        void* alo, void* bhi, void* blo, unsigned int* err, cudaStream_t st);
 cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const unsigned long long* h_lbase,
                                const unsigned long long* h_kp, void* ahi, void* alo, void* bhi, void* blo,
                                double* partial, int nsplit, unsigned int* err, bool inject_stall,

@@ -108,6 +108,26 @@ __device__ __forceinline__ void cheb_seq(float* T, float z2) {
   }
 }
 
+// (x + i y)^E, E >= 1, by repeated squaring: a pass that starts at column
+// m0 needs the power m0, in about 4 log2(m0) instructions instead of 4 m0.
+template <int E>
+__device__ __forceinline__ void cpow(float x, float y, float& r, float& i) {
+  if constexpr (E == 1) {
+    r = x;
+    i = y;
+  } else if constexpr (E % 2 == 0) {
+    float a, b;
+    cpow<E / 2>(x, y, a, b);
+    r = fmaf(a, a, -(b * b));
+    i = (a + a) * b;
+  } else {
+    float a, b;
+    cpow<E - 1>(x, y, a, b);
+    r = fmaf(a, x, -(b * y));
+    i = fmaf(a, y, b * x);
+  }
+}
+
 // Add one neighbour (weight w, unit direction x, y, z) to the pass's
 // accumulators: one FMA per coefficient, plus the Chebyshev sequence (shared
 // by all Chebyshev columns), the Legendre recurrences of the other columns,
@@ -131,14 +151,9 @@ __device__ __forceinline__ void accum_pass(const AlmArgs& a, float* acc, float w
   constexpr int MS = M0 < 1 ? 1 : M0;
   constexpr int ME = M1 < L ? M1 : L;
   if constexpr (MS <= ME) {
-    float cr = w * x, ci = w * y;  // w (x + i y)^1
-#pragma unroll
-    for (int k = 1; k < MS; ++k) {
-      const float t = fmaf(cr, x, -(ci * y));
-      ci = fmaf(cr, y, ci * x);
-      cr = t;
-    }
-    columns_rec<L, M0, M1, MS, ME>(a, acc, T, x, y, z, cr, ci);
+    float pr, pi;
+    cpow<MS>(x, y, pr, pi);  // (x + i y)^MS by squaring
+    columns_rec<L, M0, M1, MS, ME>(a, acc, T, x, y, z, w * pr, w * pi);
   }
 }
 
