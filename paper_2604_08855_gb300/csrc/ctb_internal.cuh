@@ -259,6 +259,7 @@ struct AlmArgs {
   unsigned long long* work;
   int nbins;
   int row;
+  int pass;                       // 3-D: the m-pass this launch runs (one launch per pass)
   float sph_origin[3];            // sphere mode: the points' position = origin + unit * (x, y, z)
   float sph_unit;
   float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];  // recurrence beta_lm at [l*(kLmaxCap+1)+m]

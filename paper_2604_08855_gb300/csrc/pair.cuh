@@ -243,9 +243,9 @@ __device__ __forceinline__ Prefetch prefetch_start(const uint32_t* lists, const 
 template <int L, int M0, int M1>
 struct Step3D {
   static constexpr int NCP = round32(coef_count(L, M0, M1));
-  // Only kernels with a single m-pass take the full-lane copy of the step:
-  // with several passes the extra code no longer fits the instruction cache.
-  static constexpr bool kFullLaneLoop = pass_end(L, 0, pass_cap(L, 0)) >= L;
+  // Each launch runs one m-pass, so the full-lane copy of the step and the
+  // general one are the only code in the instruction cache.
+  static constexpr bool kFullLaneLoop = true;
   const AlmArgs& a;
   __device__ __forceinline__ void operator()(float* acc, float w, float dx, float dy, float dz) const {
     const float ir = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
@@ -358,19 +358,42 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
   run_steps(a, Step3D<L, M0, M1>{a}, cur, nxt, P, pf, out, base, sbuf, lane, pe);
 }
 
-// The m-range passes of one bin (bin-major: a bin's run is re-read by each
-// pass while it is still in L1); the last pass prefetches the next bin's run.
+// The m-range passes of kernel L run as separate launches, one pass each:
+// launch `pass` runs that pass over every non-empty bin of each primary, so
+// all warps on the GPU execute the same pass's code.  (With all passes in one
+// launch, warps in different passes overflowed the instruction cache.)  The
+// lists are re-read once per pass; the points stay in L2.
 template <int L, int M0, int BASE>
-struct PassChain {
+struct PassSel {
   static constexpr int M1 = pass_end(L, M0, pass_cap(L, M0));
   static constexpr int NCP = round32(coef_count(L, M0, M1));
   static constexpr bool LAST = M1 + 1 > L;
-  __device__ static __forceinline__ void run(const AlmArgs& a, Run cur, Run nxt_bin, const uint4 P, Prefetch& pf,
-                                             float* out, float* sbuf, int lane, uint32_t pe) {
-    run_pass<L, M0, M1>(a, cur, LAST ? nxt_bin : cur, P, pf, out + BASE, BASE, sbuf, lane, pe);
-    if constexpr (!LAST) PassChain<L, M1 + 1, BASE + NCP>::run(a, cur, nxt_bin, P, pf, out, sbuf, lane, pe);
+  __device__ static __forceinline__ void run(const AlmArgs& a, int pass, Run cur, Run nxt, int b, int nb,
+                                             const uint32_t* s_off, const uint32_t* s_n, const uint4 P, float* mrow,
+                                             float* sbuf, int lane, uint32_t pe) {
+    if (LAST || pass == 0) {  // the last pass needs no test (a single-pass kernel has only it)
+      Prefetch pf = prefetch_start(a.lists, a.pts, cur, nxt, P, lane);
+      while (true) {
+        run_pass<L, M0, M1>(a, cur, nxt, P, pf, mrow + (size_t)b * a.row + BASE, BASE, sbuf, lane, pe);
+        b = nb;
+        if (b >= a.nbins) break;
+        cur = nxt;
+        nb = b + 1;
+        while (nb < a.nbins && s_n[nb] == 0) ++nb;
+        nxt = nb < a.nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
+      }
+    } else if constexpr (!LAST) {
+      PassSel<L, M1 + 1, BASE + NCP>::run(a, pass - 1, cur, nxt, b, nb, s_off, s_n, P, mrow, sbuf, lane, pe);
+    }
   }
 };
+
+// number of m-passes of kernel L
+__host__ __device__ constexpr int pass_count(int L) {
+  int n = 0;
+  for (int m0 = 0; m0 <= L; m0 = pass_end(L, m0, pass_cap(L, m0)) + 1) ++n;
+  return n;
+}
 
 // largest per-pass accumulator count of kernel L (sizes the flush buffer)
 __host__ __device__ constexpr int max_ncp(int L) {
@@ -393,8 +416,9 @@ constexpr size_t alm_smem_per_warp() {
 }
 
 // One warp per primary: its (primary, bin) lists are consecutive runs of the
-// lists buffer; each list is accumulated in registers and flushed once per
-// m-pass, with the next list's first loads already in flight.
+// lists buffer; each list is accumulated in registers for this launch's
+// m-pass and flushed once, with the next list's first loads already in
+// flight.
 template <int L>
 __global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
   extern __shared__ float s_alm[];
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
       const uint32_t n = __ldg(a.counts + ib + b);
       s_n[b] = n;
       s_off[b] = __ldg(a.offsets + ib + b);
-      if (n == 0) {
+      if (n == 0 && (pass_count(L) == 1 || a.pass == 0)) {
         // empty bin: its row is zero
         float4* o = reinterpret_cast<float4*>(a.M + (ib + b) * (uint64_t)a.row);
         for (int k = 0; k < a.row / 4; ++k) o[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -436,30 +460,45 @@ __global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
       const uint32_t pe = s_off[nbins - 1] + s_n[nbins - 1];
       if (lane < (int)kListPrefetchLines && cur.off + (uint32_t)lane * 32u < pe)
         prefetch_l2(a.lists + cur.off + (uint32_t)lane * 32u);
-      // the first pass continues into the same bin when more m-passes follow
-      Prefetch pf = prefetch_start(a.lists, a.pts, cur, PassChain<L, 0, 0>::LAST ? nxt : cur, P, lane);
-      while (true) {
-        PassChain<L, 0, 0>::run(a, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, sbuf, lane, pe);
-        b = nb;
-        if (b >= nbins) break;
-        cur = nxt;
-        nb = b + 1;
-        while (nb < nbins && s_n[nb] == 0) ++nb;
-        nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
+      if constexpr (pass_count(L) == 1) {
+        Prefetch pf = prefetch_start(a.lists, a.pts, cur, nxt, P, lane);
+        while (true) {
+          run_pass<L, 0, L>(a, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, 0, sbuf, lane, pe);
+          b = nb;
+          if (b >= nbins) break;
+          cur = nxt;
+          nb = b + 1;
+          while (nb < nbins && s_n[nb] == 0) ++nb;
+          nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
+        }
+      } else {
+        PassSel<L, 0, 0>::run(a, a.pass, cur, nxt, b, nb, s_off, s_n, P, a.M + ib * (uint64_t)a.row, sbuf, lane,
+                              pe);
       }
     }
     __syncwarp();  // s_n / s_off are rewritten for the next primary
   }
 }
 
+// one launch per m-pass, each with the work counter zeroed first
 template <int L>
 cudaError_t launch_alm_L(const AlmArgs& a, int wpb, int nblocks, cudaStream_t st) {
   const size_t smem = (size_t)wpb * alm_smem_per_warp<L>();
   cudaError_t e = cudaFuncSetAttribute(k_alm<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_alm<L><<<nblocks, wpb * 32, smem, st>>>(a);
-  ++g_launches;
-  return cudaGetLastError();
+  AlmArgs ap = a;
+  for (int p = 0; p < pass_count(L); ++p) {
+    ap.pass = p;
+    if (p > 0) {
+      e = cudaMemsetAsync(ap.work, 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return e;
+    }
+    k_alm<L><<<nblocks, wpb * 32, smem, st>>>(ap);
+    ++g_launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <int L>
