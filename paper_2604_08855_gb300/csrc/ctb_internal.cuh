@@ -98,9 +98,61 @@ __host__ __device__ constexpr int pass_end(int L, int m0, int cap) {
   return m - 1;
 }
 
+// Columns accumulated as Chebyshev moments: m <= cheb_max_m(L).  Above it
+// the monic Legendre recurrence is used (its conditioning does not degrade
+// with m; the moment conversion does).
+__host__ __device__ constexpr int cheb_max_m(int L) { return L <= 10 ? L : 3; }
+
+// The passes are balanced by an estimate of their FP32 instructions per
+// neighbour: one per Chebyshev-moment coefficient, two per Legendre-
+// recurrence coefficient, the Chebyshev sequence T_k(z) (one per degree) in
+// the pass that starts with a Chebyshev column, and kPassOverhead for the
+// neighbour's load, direction and the flush.  The number of passes stays that
+// of filling each to kPassCap accumulators.
+constexpr int kPassOverhead = 40;
+
+__host__ __device__ constexpr int col_cost(int L, int m) {
+  return (L - m + 1) * (m == 0 ? 1 : 2) * (m <= cheb_max_m(L) ? 1 : 2);
+}
+
+// end column of the pass starting at m0: columns are added while the pass
+// holds at most kPassCap coefficients and costs at most `budget`
+__host__ __device__ constexpr int pass_end_budget(int L, int m0, int budget) {
+  int s = 0, cost = kPassOverhead + (m0 <= cheb_max_m(L) ? L - m0 : 0), m = m0;
+  while (m <= L) {
+    const int c = (L - m + 1) * (m == 0 ? 1 : 2);
+    if ((s + c > kPassCap || cost + col_cost(L, m) > budget) && m > m0) break;
+    s += c;
+    cost += col_cost(L, m);
+    ++m;
+  }
+  return m - 1;
+}
+
+__host__ __device__ constexpr int passes_with_budget(int L, int budget) {
+  int n = 0;
+  for (int m0 = 0; m0 <= L; m0 = pass_end_budget(L, m0, budget) + 1) ++n;
+  return n;
+}
+
+// the smallest budget that keeps the pass count of the plain fill
+__host__ __device__ constexpr int pass_budget(int L) {
+  const int target = passes_with_budget(L, 1 << 30);
+  int lo = 0, hi = 1 << 20;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (passes_with_budget(L, mid) <= target) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
 // accumulator slots of the m-range pass of the pair kernel for ell_max L that
-// starts at column m0
-__host__ __device__ constexpr int pass_cap(int L, int m0) { return (void)L, (void)m0, kPassCap; }
+// starts at column m0 (pass_end with this cap ends the pass where the
+// balanced split does)
+__host__ __device__ constexpr int pass_cap(int L, int m0) {
+  return coef_count(L, m0, pass_end_budget(L, m0, pass_budget(L)));
+}
 
 __host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
 

@@ -40,10 +40,6 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Columns accumulated as Chebyshev moments: m <= cheb_max_m(L).  Above it
-// the monic Legendre recurrence is used (its conditioning does not degrade
-// with m; the moment conversion does).
-__host__ __device__ constexpr int cheb_max_m(int L) { return L <= 10 ? L : 3; }
 
 // Column m >= 1 of the Legendre recurrence, l = LL..L (template recursion keeps
 // every accumulator index a compile-time constant, so the array stays in
