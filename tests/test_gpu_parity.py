@@ -71,13 +71,27 @@ def test_uniform_20k_full_vs_oracle(ctbmod):
     assert zeta_err(z, ref) < TOL_FP32
 
 
-@pytest.mark.parametrize("lmax", [12, 20])
+@pytest.mark.parametrize("lmax", [11, 12, 13, 14, 16, 17, 18, 20])
 def test_multipass_lmax_vs_oracle(ctbmod, lmax):
     xyz, w = synth.thomas(3000, 300.0, 30, 5.0, seed=23, weights="u0.5-1.5")
     kw = dict(box=300.0, rmin=3.0, rmax=50.0, nbins=5, lmax=lmax)
     z, est = run_full(ctbmod, xyz, w, kw)
     ref = oracle.zeta(xyz, w, **kw)
     assert zeta_err(z, ref) < TOL_FP32
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16X3", "TF32"])
+def test_caps_nbins64_lmax20_vs_oracle(ctbmod, prec):
+    """The largest bin count and multipole order together, in every precision."""
+    xyz, w = synth.thomas(2500, 200.0, 25, 6.0, seed=25, weights="u0.5-1.5")
+    kw = dict(box=200.0, rmin=1.0, rmax=60.0, nbins=ctbmod.NBINS_CAP, lmax=ctbmod.LMAX_CAP)
+    est = make(ctbmod, **kw)
+    est.set_option(ctbmod.OPT_PRECISION, getattr(ctbmod, "PREC_" + prec))
+    est.set_points(xyz, w)
+    z = est.compute()
+    ref = oracle.zeta(xyz, w, **kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < (TOL_FP32 if prec == "FP32" else 1e-3)
 
 
 def test_alm_vs_oracle(ctbmod):
