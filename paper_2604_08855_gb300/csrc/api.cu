@@ -362,6 +362,9 @@ void finish_geom(ctb_ctx* c, Geom& g, uint32_t nc) {
   g.cell_scale = (float)(nc / std::ldexp(1.0, g.shift));
   g.rcell = (float)(rmax_u * nc / std::ldexp(1.0, g.shift) * (1.0 + 1e-5) + 1e-3);
   g.general = c->sphere;
+  g.half_unit = (float)(0.5 * c->unit);
+  g.tmin = (float)c->tmin;
+  g.inv_dt = c->sphere ? (float)(c->nbins / (c->tmax - c->tmin)) : 0.f;
 }
 
 int bits_for(uint32_t ncells) {

@@ -44,9 +44,10 @@ struct Geom {
   float inv_dr_u;      // nbins / (r_max - r_min) in 1/units
   float rcell;         // r_max in cell units, padded by a small slack
   float cell_scale;    // nc / 2^shift : units -> cell units
-  int general;         // 1: bin edges not linear in r (sphere: chords of linear angles);
-                       //    rmin_u / inv_dr_u give only a first guess, the exact
-                       //    thresholds decide every candidate
+  int general;         // 1: bin edges not linear in r (sphere: chords of linear angles)
+  float half_unit;     // sphere: unit / 2, so that chord / 2 = r_units * half_unit
+  float tmin;          // sphere: theta_min (radians)
+  float inv_dt;        // sphere: nbins / (theta_max - theta_min)
 };
 
 // Rows of the neighbour scan: W x W x-rows of cells at (dy, dz) offsets

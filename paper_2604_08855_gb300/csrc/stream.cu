@@ -21,6 +21,8 @@
 //          lanes that share a bin)
 // The kernel holds few registers, so many warps per SM hide the load latency
 // that dominates this phase.
+#include <algorithm>
+
 #include "ctb_internal.cuh"
 
 namespace ctb {
@@ -106,7 +108,8 @@ __device__ __forceinline__ void row_ranges(const StreamArgs& a, const Geom& g, c
   }
 }
 
-template <bool FILL>
+// GEN: bin edges not linear in r (the sphere's angle bins), count pass only
+template <bool FILL, bool GEN>
 __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
   extern __shared__ uint32_t s_cnt_all[];
   const int lane = threadIdx.x & 31;
@@ -242,13 +245,25 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
             int b = 0;
             if (inb) {
               const float r = r2 * rsqrtf(r2);
-              const float tt = (r - g.rmin_u) * g.inv_dr_u;
+              float tt, guard;
+              if constexpr (GEN) {
+                // sphere: the bin of theta = 2 asin(chord / 2).  Its float
+                // error stays below 1e-6 theta while chord / 2 <= 0.99 (asin
+                // is ill-conditioned towards 1); the guard is ten times that,
+                // and larger chords always take the exact test.
+                const float x = r * g.half_unit;
+                const float th = 2.f * asinf(fminf(x, 1.f));
+                tt = (th - g.tmin) * g.inv_dt;
+                guard = x > 0.99f ? 1.f : fmaxf(1e-4f, fmaf(1e-5f, th, 1e-7f) * g.inv_dt);
+              } else {
+                tt = (r - g.rmin_u) * g.inv_dr_u;
+                guard = 1e-4f;
+              }
               b = (int)floorf(tt);
               const float fr = tt - (float)b;
-              if (g.general || (unsigned)b >= (unsigned)nbins || fabsf(fr - 0.5f) > 0.5f - 1e-4f) {
-                // within float rounding of an edge (or edges not linear in r,
-                // where b is only a first guess): exact integer r^2 vs exact
-                // thresholds
+              if ((unsigned)b >= (unsigned)nbins || fabsf(fr - 0.5f) > 0.5f - guard) {
+                // within float rounding of an edge: exact integer r^2 vs
+                // exact thresholds
                 const unsigned long long e2 = (unsigned long long)((long long)ix * ix + (long long)iy * iy +
                                                                    (long long)iz * iz);
                 if (e2 == 0ull || e2 < __ldg(a.thr) || e2 >= __ldg(a.thr + nbins)) {
@@ -289,26 +304,44 @@ static size_t stream_smem(bool fill, int nbins) {
 }
 
 int stream_blocks_per_sm(bool fill, int nbins) {
+  // the two count kernels differ only in the binning arithmetic; the linear one sizes the launch
   int nb = 0;
   const size_t smem = stream_smem(fill, nbins);
   if (!fill && smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      cudaFuncSetAttribute(k_stream<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
     return 0;
-  cudaError_t e = fill ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<true>, kStreamThreads, smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<false>, kStreamThreads, smem);
-  return e == cudaSuccess ? nb : 0;
+  cudaError_t e =
+      fill ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<true, false>, kStreamThreads, smem)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<false, false>, kStreamThreads, smem);
+  int ng = nb;
+  if (!fill) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_stream<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ng, k_stream<false, true>, kStreamThreads, smem) !=
+        cudaSuccess)
+      return 0;
+  }
+  return e == cudaSuccess ? std::min(nb, ng) : 0;
 }
 
 cudaError_t launch_stream(const StreamArgs& a, bool fill, int nblocks, cudaStream_t st) {
   const size_t smem = stream_smem(fill, a.g.nbins);
-  if (!fill && smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  if (fill) {
+    k_stream<true, false><<<nblocks, kStreamThreads, smem, st>>>(a);
+  } else {
+    const void* fn = a.g.general ? (const void*)k_stream<false, true> : (const void*)k_stream<false, false>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    if (a.g.general)
+      k_stream<false, true><<<nblocks, kStreamThreads, smem, st>>>(a);
+    else
+      k_stream<false, false><<<nblocks, kStreamThreads, smem, st>>>(a);
   }
-  if (fill)
-    k_stream<true><<<nblocks, kStreamThreads, smem, st>>>(a);
-  else
-    k_stream<false><<<nblocks, kStreamThreads, smem, st>>>(a);
   ++g_launches;
   return cudaGetLastError();
 }
