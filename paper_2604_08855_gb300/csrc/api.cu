@@ -550,8 +550,8 @@ double mean_neighbours(const ctb_ctx* c) {
 int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   int wpb = c->wpb > 0 ? c->wpb : 4;
   int bps = c->sphere ? am_blocks_per_sm(c->lmax, wpb) : alm_blocks_per_sm(c->Lk, wpb);
-  int sbps = stream_blocks_per_sm(true, c->nbins);
-  int cbps = stream_blocks_per_sm(false, c->nbins);
+  int sbps = stream_blocks_per_sm(true, c->nbins, false);
+  int cbps = stream_blocks_per_sm(false, c->nbins, c->sphere != 0);
   if (bps < 1 || sbps < 1 || cbps < 1) return fail(c, CTB_ERR_CUDA, "pair kernels cannot be resident");
   pl->wpb = wpb;
   pl->alm_blocks = bps * c->nsm;

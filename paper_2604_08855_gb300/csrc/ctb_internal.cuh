@@ -292,7 +292,7 @@ struct StreamArgs {
   unsigned long long* code_base;  // [prim_count][row_blocks] start of each row block's codes
   Geom g;
 };
-int stream_blocks_per_sm(bool fill, int nbins);
+int stream_blocks_per_sm(bool fill, int nbins, bool general);
 cudaError_t launch_stream(const StreamArgs& a, bool fill, int nblocks, cudaStream_t st);
 constexpr int kStreamThreads = 256;
 

@@ -303,28 +303,14 @@ static size_t stream_smem(bool fill, int nbins) {
   return (size_t)(kStreamThreads / 32) * (fill ? kNbinsCap : nbins * 32) * sizeof(uint32_t);
 }
 
-int stream_blocks_per_sm(bool fill, int nbins) {
-  // the two count kernels differ only in the binning arithmetic; the linear one sizes the launch
-  int nb = 0;
+int stream_blocks_per_sm(bool fill, int nbins, bool general) {
+  const void* fn = fill ? (const void*)k_stream<true, false>
+                        : (general ? (const void*)k_stream<false, true> : (const void*)k_stream<false, false>);
   const size_t smem = stream_smem(fill, nbins);
-  if (!fill && smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_stream<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
-  cudaError_t e =
-      fill ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<true, false>, kStreamThreads, smem)
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream<false, false>, kStreamThreads, smem);
-  int ng = nb;
-  if (!fill) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_stream<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-      return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ng, k_stream<false, true>, kStreamThreads, smem) !=
-        cudaSuccess)
-      return 0;
-  }
-  return e == cudaSuccess ? std::min(nb, ng) : 0;
+  int nb = 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kStreamThreads, smem) == cudaSuccess ? nb : 0;
 }
 
 cudaError_t launch_stream(const StreamArgs& a, bool fill, int nblocks, cudaStream_t st) {
