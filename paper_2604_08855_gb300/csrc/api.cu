@@ -352,7 +352,10 @@ int upload_thresholds(ctb_ctx* c) {
 // float geometry of the grid and bins from c->unit, nc and g.shift
 void finish_geom(ctb_ctx* c, Geom& g, uint32_t nc) {
   g.nc = nc;
-  g.ncells = nc * nc * nc;
+  uint32_t xs = kXSub;
+  while (xs > 1 && (uint64_t)nc * nc * nc * xs >= ((uint64_t)1 << 31)) xs >>= 1;
+  g.ncx = nc * xs;
+  g.ncells = nc * nc * g.ncx;
   const double rmin_u = c->rmin / c->unit, rmax_u = c->rmax / c->unit;
   // the float pre-filter; never 0, so that it also rejects r = 0
   g.rlo2_u = std::max((float)(rmin_u * rmin_u * (1.0 - 1e-5)), 0.25f);

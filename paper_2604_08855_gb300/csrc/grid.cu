@@ -44,9 +44,9 @@ __global__ void k_ingest(const double* __restrict__ xyz, const double* __restric
         if (!(s < 2147483647.0)) s = 2147483647.0;
       }
       u[k] = (uint32_t)s;
-      c[k] = (uint32_t)(((uint64_t)u[k] * g.nc) >> g.shift);
+      c[k] = (uint32_t)(((uint64_t)u[k] * (k == 0 ? g.ncx : g.nc)) >> g.shift);
     }
-    key[i] = key_base + (c[2] * g.nc + c[1]) * g.nc + c[0];
+    key[i] = key_base + (c[2] * g.nc + c[1]) * g.ncx + c[0];
     val[i] = val_base + (uint32_t)i;
     pts[i] = make_uint4(u[0], u[1], u[2], __float_as_uint((float)wi));
   }

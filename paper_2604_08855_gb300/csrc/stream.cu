@@ -47,7 +47,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 struct RowWin {
   int W, off0, nrows;
   bool fullwin;
-  float R2, fx, fry, frz;  // (r_max in cell units)^2, primary's position in cell units
+  float R2, fx, fry, frz;  // (r_max in cell units)^2; primary's x in x-cell units, y and z fractions
+  float xs;                // x-cells per cell (ncx / nc)
   int cxp, cyp, czp;
   uint32_t cbase;
 };
@@ -75,28 +76,31 @@ __device__ __forceinline__ void row_ranges(const StreamArgs& a, const Geom& g, c
     ok = ok && cy >= 0 && cy < (int)nc && cz >= 0 && cz < (int)nc;
   }
   if (!ok) return;
-  const float hw = sqrtf(rw.R2 - rho2);
+  // the row's x-range in x-cells (a row is split xs times finer along x
+  // than across, so its ends overshoot the ball by less)
+  const float hw = sqrtf(rw.R2 - rho2) * rw.xs;
+  const int nx = (int)g.ncx;
   int lo = (int)floorf(rw.fx - hw), hi = (int)floorf(rw.fx + hw);
-  const uint32_t rb = rw.cbase + ((uint32_t)cz * nc + (uint32_t)cy) * nc;
+  const uint32_t rb = rw.cbase + ((uint32_t)cz * nc + (uint32_t)cy) * (uint32_t)nx;
   int a0 = 1, b0 = 0, a1 = 1, b1 = 0;
   if (g.periodic) {
-    if (hi - lo + 1 >= (int)nc) {
+    if (hi - lo + 1 >= nx) {
       a0 = 0;
-      b0 = (int)nc - 1;
+      b0 = nx - 1;
     } else {
-      const int lm = pmod(lo, (int)nc), hm = pmod(hi, (int)nc);
+      const int lm = pmod(lo, nx), hm = pmod(hi, nx);
       a0 = lm;
       if (lm <= hm) {
         b0 = hm;
       } else {
-        b0 = (int)nc - 1;
+        b0 = nx - 1;
         a1 = 0;
         b1 = hm;
       }
     }
   } else {
     a0 = max(lo, 0);
-    b0 = min(hi, (int)nc - 1);
+    b0 = min(hi, nx - 1);
   }
   if (a0 <= b0) {
     s0 = __ldg(a.cell_start + rb + a0);
@@ -122,6 +126,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
   const uint32_t nc = g.nc;
   RowWin rw;
   rw.R2 = g.rcell * g.rcell;
+  rw.xs = (float)(g.ncx / nc);
   {
     const RowWindow win = row_window(g);
     rw.W = win.W;
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
     }
     __syncwarp();
 
-    const uint64_t sx = (uint64_t)P.x * nc, sy = (uint64_t)P.y * nc, sz = (uint64_t)P.z * nc;
+    const uint64_t sx = (uint64_t)P.x * g.ncx, sy = (uint64_t)P.y * nc, sz = (uint64_t)P.z * nc;
     rw.cxp = (int)(sx >> g.shift);
     rw.cyp = (int)(sy >> g.shift);
     rw.czp = (int)(sz >> g.shift);
