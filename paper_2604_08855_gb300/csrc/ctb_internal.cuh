@@ -33,14 +33,14 @@ constexpr int kPassCap = 128;
 
 // A row of cells (fixed y, z) is split this many times finer along x than
 // across: a primary's scan of a row then starts and ends closer to its ball
-// (at 6 cells per r_max, about 8 % fewer candidates) at no extra rows.
-constexpr uint32_t kXSub = 4;
+// (at 6 cells per r_max, about 9 % fewer candidates) at no extra rows.
+constexpr uint32_t kXSub = 8;
 
 struct Geom {
   int periodic;        // 1: periodic cube, 0: open space
   int shift;           // 32 (periodic) or 31 (open): unit coordinates < 2^shift
   uint32_t nc;         // cells per axis across the rows (y, z)
-  uint32_t ncx;        // cells along a row (x): nc times kXSub, or fewer for very fine grids
+  uint32_t ncx;        // cells along a row (x): nc times kXSub, or less for very fine grids
   uint32_t ncells;     // nc * nc * ncx
   int nbins;
   int lmax;            // requested ell_max
