@@ -748,7 +748,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     if (c->sphere)
       CK(c, launch_am(aa, c->lmax, pl.wpb, pl.alm_blocks, c->st));
     else
-      CK(c, launch_alm(aa, c->Lk, pl.wpb, pl.alm_blocks, c->st));
+      CK(c, launch_alm(aa, c->Lk, pl.wpb, c->nsm, c->st));
     CK(c, cudaEventRecord(ev[3], c->st));
     if (contract) {
       // split the chunk at catalogue boundaries (a batch): each piece adds to its catalogue's partials

@@ -318,7 +318,6 @@ struct AlmArgs {
   unsigned long long* work;
   int nbins;
   int row;
-  int pass;                       // 3-D: the m-pass this launch runs (one launch per pass)
   float sph_origin[3];            // sphere mode: the points' position = origin + unit * (x, y, z)
   float sph_unit;
   float beta[(kLmaxCap + 1) * (kLmaxCap + 1)];  // recurrence beta_lm at [l*(kLmaxCap+1)+m]
@@ -327,7 +326,8 @@ int alm_blocks_per_sm(int lmax_kernel, int warps_per_block);
 // sphere.cu: projected multipoles m = 0..mmax (mmax <= CTB_MMAX_CAP)
 int am_blocks_per_sm(int mmax, int warps_per_block);
 cudaError_t launch_am(const AlmArgs& a, int mmax, int warps_per_block, int nblocks, cudaStream_t st);
-cudaError_t launch_alm(const AlmArgs& a, int lmax_kernel, int warps_per_block, int nblocks, cudaStream_t st);
+// one launch per m-pass, each sized from its own occupancy on nsm SMs
+cudaError_t launch_alm(const AlmArgs& a, int lmax_kernel, int warps_per_block, int nsm, cudaStream_t st);
 
 // contract.cu
 struct ContractArgs {

@@ -354,75 +354,51 @@ __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, con
   run_steps(a, Step3D<L, M0, M1>{a}, cur, nxt, P, pf, out, base, sbuf, lane, pe);
 }
 
-// The m-range passes of kernel L run as separate launches, one pass each:
-// launch `pass` runs that pass over every non-empty bin of each primary, so
-// all warps on the GPU execute the same pass's code.  (With all passes in one
-// launch, warps in different passes overflowed the instruction cache.)  The
-// lists are re-read once per pass; the points stay in L2.
-template <int L, int M0, int BASE>
-struct PassSel {
-  static constexpr int M1 = pass_end(L, M0, pass_cap(L, M0));
-  static constexpr int NCP = round32(coef_count(L, M0, M1));
-  static constexpr bool LAST = M1 + 1 > L;
-  __device__ static __forceinline__ void run(const AlmArgs& a, int pass, Run cur, Run nxt, int b, int nb,
-                                             const uint32_t* s_off, const uint32_t* s_n, const uint4 P, float* mrow,
-                                             float* sbuf, int lane, uint32_t pe) {
-    if (LAST || pass == 0) {  // the last pass needs no test (a single-pass kernel has only it)
-      Prefetch pf = prefetch_start(a.lists, a.pts, cur, nxt, P, lane);
-      while (true) {
-        run_pass<L, M0, M1>(a, cur, nxt, P, pf, mrow + (size_t)b * a.row + BASE, BASE, sbuf, lane, pe);
-        b = nb;
-        if (b >= a.nbins) break;
-        cur = nxt;
-        nb = b + 1;
-        while (nb < a.nbins && s_n[nb] == 0) ++nb;
-        nxt = nb < a.nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
-      }
-    } else if constexpr (!LAST) {
-      PassSel<L, M1 + 1, BASE + NCP>::run(a, pass - 1, cur, nxt, b, nb, s_off, s_n, P, mrow, sbuf, lane, pe);
-    }
-  }
-};
-
-// number of m-passes of kernel L
+// number of m-passes of kernel L, and the columns and row offset of pass P
 __host__ __device__ constexpr int pass_count(int L) {
   int n = 0;
   for (int m0 = 0; m0 <= L; m0 = pass_end(L, m0, pass_cap(L, m0)) + 1) ++n;
   return n;
 }
-
-// largest per-pass accumulator count of kernel L (sizes the flush buffer)
-__host__ __device__ constexpr int max_ncp(int L) {
-  int best = 0;
-  for (int m0 = 0; m0 <= L;) {
-    int m1 = pass_end(L, m0, pass_cap(L, m0));
-    int v = round32(coef_count(L, m0, m1));
-    if (v > best) best = v;
-    m0 = m1 + 1;
-  }
-  return best;
+__host__ __device__ constexpr int pass_m0(int L, int P) {
+  int m0 = 0;
+  for (int p = 0; p < P; ++p) m0 = pass_end(L, m0, pass_cap(L, m0)) + 1;
+  return m0;
+}
+__host__ __device__ constexpr int pass_m1(int L, int P) { return pass_end(L, pass_m0(L, P), pass_cap(L, pass_m0(L, P))); }
+__host__ __device__ constexpr int pass_ncp(int L, int P) { return round32(coef_count(L, pass_m0(L, P), pass_m1(L, P))); }
+__host__ __device__ constexpr int pass_base(int L, int P) {
+  int b = 0;
+  for (int p = 0; p < P; ++p) b += pass_ncp(L, p);
+  return b;
 }
 
-// resident blocks of 4 warps the register budget is sized for
-__host__ __device__ constexpr int alm_min_blocks(int L) { return max_ncp(L) <= 64 ? 5 : (max_ncp(L) <= 96 ? 4 : 3); }
+// resident blocks of 4 warps the register budget of a pass is sized for
+__host__ __device__ constexpr int alm_min_blocks(int ncp) { return ncp <= 64 ? 5 : (ncp <= 96 ? 4 : 3); }
 
-template <int L>
-constexpr size_t alm_smem_per_warp() {
-  return (size_t)32 * (max_ncp(L) + 4) * sizeof(float) + 2 * kNbinsCap * sizeof(uint32_t);
+__host__ __device__ constexpr size_t alm_smem_per_warp(int ncp) {
+  return (size_t)32 * (ncp + 4) * sizeof(float) + 2 * kNbinsCap * sizeof(uint32_t);
 }
 
 // One warp per primary: its (primary, bin) lists are consecutive runs of the
-// lists buffer; each list is accumulated in registers for this launch's
-// m-pass and flushed once, with the next list's first loads already in
-// flight.
-template <int L>
-__global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
+// lists buffer; each list is accumulated in registers for m-pass P of kernel
+// L and flushed once, with the next list's first loads already in flight.
+//
+// The passes of a kernel with several (l_max > 10) are separate kernels,
+// launched one after another.  With all passes in one launch, warps in
+// different passes overflowed the instruction cache; as separate kernels
+// every warp on the GPU runs the same pass body, and each pass gets its own
+// register budget (a pass with fewer accumulators runs more warps per SM).
+// The lists are re-read once per pass; the points stay in L2.
+template <int L, int P>
+__global__ void __launch_bounds__(128, alm_min_blocks(pass_ncp(L, P))) k_alm(AlmArgs a) {
+  constexpr int M0 = pass_m0(L, P), M1 = pass_m1(L, P), NCP = pass_ncp(L, P), BASE = pass_base(L, P);
   extern __shared__ float s_alm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  char* wbase = reinterpret_cast<char*>(s_alm) + (size_t)warp * alm_smem_per_warp<L>();
+  char* wbase = reinterpret_cast<char*>(s_alm) + (size_t)warp * alm_smem_per_warp(NCP);
   float* sbuf = reinterpret_cast<float*>(wbase);
-  uint32_t* s_off = reinterpret_cast<uint32_t*>(wbase + (size_t)32 * (max_ncp(L) + 4) * sizeof(float));
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(wbase + (size_t)32 * (NCP + 4) * sizeof(float));
   uint32_t* s_n = s_off + kNbinsCap;
   const int nbins = a.nbins;
   while (true) {
@@ -435,8 +411,8 @@ __global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
       const uint32_t n = __ldg(a.counts + ib + b);
       s_n[b] = n;
       s_off[b] = __ldg(a.offsets + ib + b);
-      if (n == 0 && (pass_count(L) == 1 || a.pass == 0)) {
-        // empty bin: its row is zero
+      if (P == 0 && n == 0) {
+        // empty bin: its row is zero (all passes' slots)
         float4* o = reinterpret_cast<float4*>(a.M + (ib + b) * (uint64_t)a.row);
         for (int k = 0; k < a.row / 4; ++k) o[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -447,7 +423,7 @@ __global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
     if (b < nbins) {
       const int64_t gi = a.prim_begin + (int64_t)i;
       const uint32_t sp = a.prim ? __ldg(a.prim + gi) : (uint32_t)gi;
-      const uint4 P = __ldg(a.pts + sp);
+      const uint4 Pt = __ldg(a.pts + sp);
       int nb = b + 1;
       while (nb < nbins && s_n[nb] == 0) ++nb;
       Run cur{s_off[b], s_n[b]};
@@ -456,55 +432,75 @@ __global__ void __launch_bounds__(128, alm_min_blocks(L)) k_alm(AlmArgs a) {
       const uint32_t pe = s_off[nbins - 1] + s_n[nbins - 1];
       if (lane < (int)kListPrefetchLines && cur.off + (uint32_t)lane * 32u < pe)
         prefetch_l2(a.lists + cur.off + (uint32_t)lane * 32u);
-      if constexpr (pass_count(L) == 1) {
-        Prefetch pf = prefetch_start(a.lists, a.pts, cur, nxt, P, lane);
-        while (true) {
-          run_pass<L, 0, L>(a, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, 0, sbuf, lane, pe);
-          b = nb;
-          if (b >= nbins) break;
-          cur = nxt;
-          nb = b + 1;
-          while (nb < nbins && s_n[nb] == 0) ++nb;
-          nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
-        }
-      } else {
-        PassSel<L, 0, 0>::run(a, a.pass, cur, nxt, b, nb, s_off, s_n, P, a.M + ib * (uint64_t)a.row, sbuf, lane,
-                              pe);
+      Prefetch pf = prefetch_start(a.lists, a.pts, cur, nxt, Pt, lane);
+      while (true) {
+        run_pass<L, M0, M1>(a, cur, nxt, Pt, pf, a.M + (ib + b) * (uint64_t)a.row + BASE, BASE, sbuf, lane, pe);
+        b = nb;
+        if (b >= nbins) break;
+        cur = nxt;
+        nb = b + 1;
+        while (nb < nbins && s_n[nb] == 0) ++nb;
+        nxt = nb < nbins ? Run{s_off[nb], s_n[nb]} : Run{0, 0};
       }
     }
     __syncwarp();  // s_n / s_off are rewritten for the next primary
   }
 }
 
-// one launch per m-pass, each with the work counter zeroed first
-template <int L>
-cudaError_t launch_alm_L(const AlmArgs& a, int wpb, int nblocks, cudaStream_t st) {
-  const size_t smem = (size_t)wpb * alm_smem_per_warp<L>();
-  cudaError_t e = cudaFuncSetAttribute(k_alm<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  AlmArgs ap = a;
-  for (int p = 0; p < pass_count(L); ++p) {
-    ap.pass = p;
-    if (p > 0) {
-      e = cudaMemsetAsync(ap.work, 0, sizeof(unsigned long long), st);
+template <int L, int P>
+int alm_occupancy_pass(int wpb) {
+  const size_t smem = (size_t)wpb * alm_smem_per_warp(pass_ncp(L, P));
+  if (cudaFuncSetAttribute(k_alm<L, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alm<L, P>, wpb * 32, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+// passes P.. of kernel L: each launch resident-sized from its own occupancy,
+// the work counter zeroed before every pass after the first
+template <int L, int P>
+cudaError_t launch_passes(const AlmArgs& a, int wpb, int nsm, cudaStream_t st) {
+  if constexpr (P >= pass_count(L)) {
+    return cudaSuccess;
+  } else {
+    const size_t smem = (size_t)wpb * alm_smem_per_warp(pass_ncp(L, P));
+    cudaError_t e = cudaFuncSetAttribute(k_alm<L, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int bps = alm_occupancy_pass<L, P>(wpb);
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    if (P > 0) {
+      e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
       if (e != cudaSuccess) return e;
     }
-    k_alm<L><<<nblocks, wpb * 32, smem, st>>>(ap);
+    k_alm<L, P><<<bps * nsm, wpb * 32, smem, st>>>(a);
     ++g_launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return launch_passes<L, P + 1>(a, wpb, nsm, st);
   }
-  return cudaSuccess;
+}
+
+template <int L>
+cudaError_t launch_alm_L(const AlmArgs& a, int wpb, int nsm, cudaStream_t st) {
+  return launch_passes<L, 0>(a, wpb, nsm, st);
+}
+
+// the smallest occupancy over the passes (0: some pass cannot be resident)
+template <int L, int P>
+int alm_occupancy_from(int wpb) {
+  if constexpr (P >= pass_count(L)) {
+    return 1 << 30;
+  } else {
+    const int o = alm_occupancy_pass<L, P>(wpb);
+    const int r = alm_occupancy_from<L, P + 1>(wpb);
+    return o < r ? o : r;
+  }
 }
 
 template <int L>
 int alm_occupancy_L(int wpb) {
-  const size_t smem = (size_t)wpb * alm_smem_per_warp<L>();
-  if (cudaFuncSetAttribute(k_alm<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alm<L>, wpb * 32, smem) != cudaSuccess) return 0;
-  return nb;
+  return alm_occupancy_from<L, 0>(wpb);
 }
 
 }  // namespace ctb

@@ -145,11 +145,11 @@ int alm_blocks_per_sm(int L, int wpb) {
   }
 }
 
-cudaError_t launch_alm(const AlmArgs& a, int L, int wpb, int nblocks, cudaStream_t st) {
+cudaError_t launch_alm(const AlmArgs& a, int L, int wpb, int nsm, cudaStream_t st) {
   switch (L) {
 #define CASE(X) \
   case X:       \
-    return launch_alm_L<X>(a, wpb, nblocks, st);
+    return launch_alm_L<X>(a, wpb, nsm, st);
     CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
     CASE(12) CASE(14) CASE(16) CASE(18) CASE(20)
 #undef CASE
