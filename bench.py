@@ -93,29 +93,72 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def _pass_end(L: int, m0: int, cap: int = 128) -> int:
-    s, m = 0, m0
+def _cheb_max_m(L: int) -> int:
+    return L if L <= 10 else 3
+
+
+def _pass_end(L: int, m0: int, budget: int, cap: int = 128) -> int:
+    """End column of the pass starting at m0, as the library splits them:
+    columns are added while the pass holds at most `cap` coefficients and its
+    estimated cost stays within `budget` (one instruction per Chebyshev
+    coefficient, two per Legendre one, the T_k sequence, 40 per neighbour)."""
+    mc = _cheb_max_m(L)
+    s, cost, m = 0, 40 + (L - m0 if m0 <= mc else 0), m0
     while m <= L:
         c = (L - m + 1) * (1 if m == 0 else 2)
-        if s + c > cap and m > m0:
+        cc = c * (1 if m <= mc else 2)
+        if (s + c > cap or cost + cc > budget) and m > m0:
             break
         s += c
+        cost += cc
         m += 1
     return m - 1
+
+
+def _passes(L: int, budget: int):
+    out, m0 = [], 0
+    while m0 <= L:
+        m1 = _pass_end(L, m0, budget)
+        out.append((m0, m1))
+        m0 = m1 + 1
+    return out
+
+
+def pass_split(L: int):
+    """The m-passes of the accumulation kernel for l_max L: the smallest cost
+    budget that keeps the pass count of filling each to 128 coefficients."""
+    target = len(_passes(L, 1 << 30))
+    lo, hi = 0, 1 << 20
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if len(_passes(L, mid)) <= target:
+            hi = mid
+        else:
+            lo = mid + 1
+    return _passes(L, lo)
+
+
+def _cpow_flops(e: int) -> int:
+    """FLOPs of (x + iy)^e by repeated squaring (FMA = 2)."""
+    if e == 1:
+        return 0
+    if e % 2 == 0:
+        return _cpow_flops(e // 2) + 5
+    return _cpow_flops(e - 1) + 6
 
 
 def flops_per_pair(lmax: int) -> int:
     """Algorithmic FP32 FLOPs per pair of the accumulation kernel (FMA = 2),
     counted from its formulation: per m-range pass the separation norm and
     direction (8), the Chebyshev sequence T_k(z) (columns m <= m_c: one FMA per
-    degree), the complex power w (x+iy)^m (6 per step), one FMA per
-    coefficient (an ADD where T_0 = 1 or the power itself is added), and the
-    monic Legendre recurrence (MUL + FMA per degree) for columns m > m_c."""
+    degree), the pass's first power w (x+iy)^m0 by squaring and one complex
+    multiplication (6) per further column, one FMA per coefficient (an ADD
+    where T_0 = 1 or the power itself is added), and the monic Legendre
+    recurrence (MUL + FMA per degree) for columns m > m_c."""
     L = lmax
-    mc = L if L <= 10 else 3
-    f, m0 = 0, 0
-    while m0 <= L:
-        m1 = _pass_end(L, m0)
+    mc = _cheb_max_m(L)
+    f = 0
+    for m0, m1 in pass_split(L):
         f += 8
         if m0 <= mc and L - m0 >= 2:
             f += 1 + 2 * (L - m0 - 1)
@@ -123,7 +166,7 @@ def flops_per_pair(lmax: int) -> int:
         if m0 == 0:
             f += 1 + 2 * L                                # column 0 (Chebyshev)
         if ms <= min(m1, L):
-            f += 2 + 6 * (ms - 1)                         # w (x+iy)^ms
+            f += 2 + _cpow_flops(ms)                      # w (x+iy)^ms
             for m in range(ms, min(m1, L) + 1):
                 if m > ms:
                     f += 6
@@ -131,7 +174,6 @@ def flops_per_pair(lmax: int) -> int:
                     f += 2 + 4 * (L - m)
                 else:
                     f += 2 + (4 if m + 1 <= L else 0) + 7 * max(0, L - m - 1)
-        m0 = m1 + 1
     return f
 
 
