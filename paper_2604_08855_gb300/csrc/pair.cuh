@@ -217,10 +217,10 @@ __device__ __forceinline__ uint32_t rec_at(const uint32_t* __restrict__ lists, R
                                            uint32_t t, int lane) {
   if (t < T) {
     const uint32_t k = t * 32 + lane;
-    return k < cur.n ? __ldcg(lists + cur.off + k) : kNone;
+    return k < cur.n ? __ldcs(lists + cur.off + k) : kNone;
   }
   const uint32_t k = (t - T) * 32 + lane;
-  return k < nxt.n ? __ldcg(lists + nxt.off + k) : kNone;
+  return k < nxt.n ? __ldcs(lists + nxt.off + k) : kNone;
 }
 
 // Loads of the first two iterations of the concatenated runs [r | nxt].
@@ -277,7 +277,7 @@ __device__ __forceinline__ void run_steps(const AlmArgs& a, const Step& step, Ru
     if (t + 3u < full) {
       // two gathers in flight: q0 = point(t), q1 = point(t + 1), j1 = word(t + 2)
       uint4 q1 = __ldg(pts + pf.j1);
-      pf.j1 = __ldcg(lists + cur.off + 64u + (uint32_t)lane);
+      pf.j1 = __ldcs(lists + cur.off + 64u + (uint32_t)lane);
       const uint32_t* __restrict__ wp = lists + cur.off + 96u + (uint32_t)lane;
       const uint32_t* pp = lists + cur.off + kListPrefetchLines * 32u;
       const bool lane0 = lane == 0;
@@ -288,7 +288,7 @@ __device__ __forceinline__ void run_steps(const AlmArgs& a, const Step& step, Ru
         const uint4 q = pf.q0;
         pf.q0 = q1;
         q1 = __ldg(pts + pf.j1);
-        pf.j1 = __ldcg(wp);
+        pf.j1 = __ldcs(wp);
         wp += 32;
         const float dx = __int2float_rn((int)(q.x - P.x));
         const float dy = __int2float_rn((int)(q.y - P.y));
@@ -341,10 +341,10 @@ __device__ __forceinline__ void run_steps(const AlmArgs& a, const Step& step, Ru
   }
   __syncwarp();
   if constexpr (V == 4) {
-    *reinterpret_cast<float4*>(o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    __stcs(reinterpret_cast<float4*>(o), make_float4(acc[0], acc[1], acc[2], acc[3]));
   } else {
 #pragma unroll
-    for (int i = 0; i < V; ++i) o[i] = acc[i];
+    for (int i = 0; i < V; ++i) __stcs(o + i, acc[i]);
   }
 }
 
