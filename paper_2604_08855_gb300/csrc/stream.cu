@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
           const uint32_t* segw = reinterpret_cast<const uint32_t*>(a.codes + seg0);
           for (uint32_t base = cs; base < ce; base += 128) {
             const uint32_t j4 = base + 4u * (uint32_t)lane;
-            const uint32_t word = j4 < ce ? segw[(j4 - cs) >> 2] : 0xffffffffu;
+            const uint32_t word = j4 < ce ? __ldcs(segw + ((j4 - cs) >> 2)) : 0xffffffffu;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const uint32_t j = j4 + (uint32_t)k;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
                 const unsigned rank = __popc(grp & lt);
                 const uint32_t c0 = cnt[b];
                 __syncwarp(act);
-                a.lists[(uint64_t)c0 + rank] = j;
+                __stcs(a.lists + ((uint64_t)c0 + rank), j);
                 if (rank == 0) cnt[b] = c0 + __popc(grp);
               }
               __syncwarp();
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
                 }
               }
             }
-            if (valid && codes_ok) a.codes[seg0 + (j - cs)] = inb ? (uint8_t)b : kNoBin;
+            if (valid && codes_ok) __stcs(a.codes + (seg0 + (j - cs)), inb ? (unsigned char)b : (unsigned char)kNoBin);
             if (inb) cnt[b * 32 + lane] += 1u;  // lane-private: no ordering, no conflict
           }
         }
