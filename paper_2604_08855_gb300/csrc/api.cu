@@ -792,6 +792,35 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
     if (cnt > 0) cand_per = std::max(1.0, (double)ctot / (double)cnt);
     double nxt = per > 0 ? 0.9 * (double)pl.list_cap / per : (double)pl.chunk_max;
     nxt = std::min(nxt, 0.9 * (double)pl.code_cap / cand_per);
+    if (seg_end && cnt > 0 && c0 < np) {
+      // a batch: the catalogues differ in size, so the pairs of a primary
+      // scale with its catalogue's size.  Learn pairs and candidates per
+      // primary per catalogue point from this chunk, and walk the next
+      // catalogues until the predicted pairs fill the buffers.
+      double pts = 0.0;  // sum over this chunk's primaries of their catalogue's size
+      for (size_t sg = 0; sg < seg_end->size(); ++sg) {
+        const int64_t s0 = sg ? (*seg_end)[sg - 1] : 0, s1 = (*seg_end)[sg];
+        const int64_t lo = std::max(s0, c0 - cnt), hi = std::min(s1, c0);
+        if (hi > lo) pts += (double)(hi - lo) * (double)(s1 - s0);
+      }
+      if (pts > 0) {
+        const double rp = (double)tot / pts, rc = (double)ctot / pts;
+        double bp = 0.9 * (double)pl.list_cap, bc = 0.9 * (double)pl.code_cap;
+        int64_t take = 0;
+        for (size_t sg = 0; sg < seg_end->size(); ++sg) {
+          const int64_t s0 = sg ? (*seg_end)[sg - 1] : 0, s1 = (*seg_end)[sg];
+          if (s1 <= c0) continue;
+          const int64_t avail = s1 - std::max(s0, c0);
+          const double pp = std::max(rp * (double)(s1 - s0), 1e-9), pc = std::max(rc * (double)(s1 - s0), 1e-9);
+          const int64_t fit = (int64_t)std::min({(double)avail, bp / pp, bc / pc});
+          take += fit;
+          bp -= (double)fit * pp;
+          bc -= (double)fit * pc;
+          if (fit < avail) break;
+        }
+        nxt = (double)take;
+      }
+    }
     C = std::max<int64_t>(1, std::min<int64_t>((int64_t)nxt, pl.chunk_max));
   }
   c->t_ms[2] = t_stream + t_alm;
@@ -958,7 +987,7 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
     return r;
   }
   const size_t zsz = (size_t)(c->lmax + 1) * c->nbins * c->nbins;
-  const size_t budget = (size_t)2 << 30;
+  const size_t budget = (size_t)8 << 30;  // FP64 partials: k catalogues x ncon rows (one wave of the contraction)
   pl.ncon = (int)std::max<size_t>(8, std::min<size_t>((size_t)pl.ncon, budget / ((size_t)k * zsz * 8)));
   const bool tc = c->precision != CTB_PREC_FP32;
   Buf& part = tc ? c->partial_tc : c->partial;
