@@ -55,6 +55,7 @@ struct ctb_ctx {
   double unit = 0;
   double origin[3] = {0, 0, 0};
   double hi[3] = {0, 0, 0};  // largest coordinate per axis (box for a periodic box)
+  double norm2_lo = 0, norm2_hi = 0;  // open space: smallest and largest |p|^2 of the catalogue
   double bbox_volume = 0;
   Layout lay{};
   int Lk = 0;
@@ -365,6 +366,18 @@ void finish_geom(ctb_ctx* c, Geom& g, uint32_t nc) {
   g.cell_scale = (float)(nc / std::ldexp(1.0, g.shift));
   g.rcell = (float)(rmax_u * nc / std::ldexp(1.0, g.shift) * (1.0 + 1e-5) + 1e-3);
   g.general = c->sphere;
+  if (c->sphere) {
+    // the shell sqrt(norm2_lo) <= |p| <= sqrt(norm2_hi) that holds every point,
+    // in cell units (centre: the origin of coordinates), padded for rounding
+    const double ycell = nc / std::ldexp(1.0, g.shift) / c->unit;  // cells per coordinate unit (y, z)
+    g.shell_c[0] = (float)(-c->origin[0] * ycell * (g.ncx / nc));
+    g.shell_c[1] = (float)(-c->origin[1] * ycell);
+    g.shell_c[2] = (float)(-c->origin[2] * ycell);
+    const double rlo = std::sqrt(std::max(c->norm2_lo, 0.0)) * ycell, rhi = std::sqrt(c->norm2_hi) * ycell;
+    const double pad = 1e-5 * rhi + 4e-3;
+    g.shell_r2lo = (float)(rlo > pad ? (rlo - pad) * (rlo - pad) : 0.0);
+    g.shell_r2hi = (float)((rhi + pad) * (rhi + pad));
+  }
   g.half_unit = (float)(0.5 * c->unit);
   g.tmin = (float)c->tmin;
   g.inv_dt = c->sphere ? (float)(c->nbins / (c->tmax - c->tmin)) : 0.f;
@@ -431,9 +444,9 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     if (n > 0) {
       int nblk = bbox_blocks(n);
-      CK(c, ensure(c, c->bbox_part, (size_t)nblk * 6 * sizeof(double)));
+      CK(c, ensure(c, c->bbox_part, (size_t)nblk * 8 * sizeof(double)));
       CK(c, launch_bbox(dxyz, n, P<double>(c->bbox_part), nblk, P<uint32_t>(c->flags), c->st));
-      std::vector<double> part((size_t)nblk * 6);
+      std::vector<double> part((size_t)nblk * 8);
       uint32_t fl = 0;
       CK(c, cudaMemcpyAsync(part.data(), c->bbox_part.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
                             c->st));
@@ -444,11 +457,16 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
         lo[k] = INFINITY;
         hi[k] = -INFINITY;
       }
-      for (int b = 0; b < nblk; ++b)
+      c->norm2_lo = INFINITY;
+      c->norm2_hi = 0.0;
+      for (int b = 0; b < nblk; ++b) {
         for (int k = 0; k < 3; ++k) {
-          lo[k] = std::min(lo[k], part[b * 6 + k]);
-          hi[k] = std::max(hi[k], part[b * 6 + 3 + k]);
+          lo[k] = std::min(lo[k], part[b * 8 + k]);
+          hi[k] = std::max(hi[k], part[b * 8 + 4 + k]);
         }
+        c->norm2_lo = std::min(c->norm2_lo, part[b * 8 + 3]);
+        c->norm2_hi = std::max(c->norm2_hi, part[b * 8 + 7]);
+      }
     }
     double ext = 0;
     c->bbox_volume = 1.0;
@@ -553,7 +571,7 @@ double mean_neighbours(const ctb_ctx* c) {
 int plan_pairs(ctb_ctx* c, int64_t np, PairPlan* pl) {
   int wpb = c->wpb > 0 ? c->wpb : 4;
   int bps = c->sphere ? am_blocks_per_sm(c->lmax, wpb) : alm_blocks_per_sm(c->Lk, wpb);
-  int sbps = stream_blocks_per_sm(true, c->nbins, false);
+  int sbps = stream_blocks_per_sm(true, c->nbins, c->sphere != 0);
   int cbps = stream_blocks_per_sm(false, c->nbins, c->sphere != 0);
   if (bps < 1 || sbps < 1 || cbps < 1) return fail(c, CTB_ERR_CUDA, "pair kernels cannot be resident");
   pl->wpb = wpb;

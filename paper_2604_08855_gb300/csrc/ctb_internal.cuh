@@ -54,6 +54,9 @@ struct Geom {
   float half_unit;     // sphere: unit / 2, so that chord / 2 = r_units * half_unit
   float tmin;          // sphere: theta_min (radians)
   float inv_dt;        // sphere: nbins / (theta_max - theta_min)
+  float shell_c[3];    // sphere: the origin of coordinates in cell units (x in x-cells)
+  float shell_r2lo;    // sphere: (smallest |p|)^2 and (largest |p|)^2 of the catalogue in
+  float shell_r2hi;    //   (y, z) cell units squared, padded: every point lies in that shell
 };
 
 // Rows of the neighbour scan: W x W x-rows of cells at (dy, dz) offsets

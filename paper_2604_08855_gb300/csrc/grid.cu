@@ -78,38 +78,42 @@ int bbox_blocks(int64_t n) {
 
 __global__ void k_bbox(const double* __restrict__ xyz, int64_t n, double* __restrict__ part,
                        uint32_t* flags) {
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  // per block: min x, y, z, |p|^2 and max x, y, z, |p|^2 of the finite points
+  double lo[4] = {INFINITY, INFINITY, INFINITY, INFINITY}, hi[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double v[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+    if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
+      atomicOr(flags, 1u);
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      double v = xyz[3 * i + k];
-      if (!isfinite(v)) {
-        atomicOr(flags, 1u);
-        continue;
-      }
-      lo[k] = fmin(lo[k], v);
-      hi[k] = fmax(hi[k], v);
+      lo[k] = fmin(lo[k], v[k]);
+      hi[k] = fmax(hi[k], v[k]);
     }
+    const double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    lo[3] = fmin(lo[3], r2);
+    hi[3] = fmax(hi[3], r2);
   }
-  __shared__ double s[6][256];
+  __shared__ double s[8][256];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     s[k][threadIdx.x] = lo[k];
-    s[3 + k][threadIdx.x] = hi[k];
+    s[4 + k][threadIdx.x] = hi[k];
   }
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < 4; ++k) {
         s[k][threadIdx.x] = fmin(s[k][threadIdx.x], s[k][threadIdx.x + h]);
-        s[3 + k][threadIdx.x] = fmax(s[3 + k][threadIdx.x], s[3 + k][threadIdx.x + h]);
+        s[4 + k][threadIdx.x] = fmax(s[4 + k][threadIdx.x], s[4 + k][threadIdx.x + h]);
       }
     }
     __syncthreads();
   }
-  if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+  if (threadIdx.x < 8) part[blockIdx.x * 8 + threadIdx.x] = s[threadIdx.x][0];
 }
 
 cudaError_t launch_bbox(const double* xyz, int64_t n, double* d_part, int nblk, uint32_t* d_flags,

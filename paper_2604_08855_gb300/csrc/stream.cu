@@ -53,8 +53,12 @@ struct RowWin {
   uint32_t cbase;
 };
 
-// The point ranges of row t of the window (up to two: periodic wrap in x);
-// empty ranges have s >= e.
+// The point ranges of row t of the window (up to two: periodic wrap in x,
+// or the two crossings of the sphere's shell); empty ranges have s >= e.
+// SHELL (sphere mode): every point lies in the shell of g.shell_r2lo ..
+// g.shell_r2hi around the origin, so a row that misses it is skipped without
+// a load, and a row that crosses it is cut to its crossings.
+template <bool SHELL>
 __device__ __forceinline__ void row_ranges(const StreamArgs& a, const Geom& g, const RowWin& rw, int t, uint32_t& s0,
                                            uint32_t& e0, uint32_t& s1, uint32_t& e1) {
   const uint32_t nc = g.nc;
@@ -83,7 +87,43 @@ __device__ __forceinline__ void row_ranges(const StreamArgs& a, const Geom& g, c
   int lo = (int)floorf(rw.fx - hw), hi = (int)floorf(rw.fx + hw);
   const uint32_t rb = rw.cbase + ((uint32_t)cz * nc + (uint32_t)cy) * (uint32_t)nx;
   int a0 = 1, b0 = 0, a1 = 1, b1 = 0;
-  if (g.periodic) {
+  if constexpr (SHELL) {
+    // distance range from the shell's axis to the row's (y, z) cross-section
+    const float ly = (float)cy - g.shell_c[1], lz = (float)cz - g.shell_c[2];
+    const float ny = ly > 0.f ? ly : (ly + 1.f < 0.f ? -(ly + 1.f) : 0.f);
+    const float nz = lz > 0.f ? lz : (lz + 1.f < 0.f ? -(lz + 1.f) : 0.f);
+    const float fy = fmaxf(fabsf(ly), fabsf(ly + 1.f)), fz = fmaxf(fabsf(lz), fabsf(lz + 1.f));
+    const float d2min = ny * ny + nz * nz, d2max = fy * fy + fz * fz;
+    if (d2min >= g.shell_r2hi) return;
+    // x offsets (x-cells) of the shell along the row: [alo, ahi] either side of the centre
+    const float ahi = sqrtf(g.shell_r2hi - d2min) * rw.xs;
+    const float alo = g.shell_r2lo > d2max ? sqrtf(g.shell_r2lo - d2max) * rw.xs : 0.f;
+    const float xl = rw.fx - hw, xh = rw.fx + hw, cx = g.shell_c[0];
+    // the ball's x-range meets the upper crossing [cx + alo, cx + ahi] and the lower one
+    const float pl = fmaxf(xl, cx + alo), ph = fminf(xh, cx + ahi);
+    const float ml = fmaxf(xl, cx - ahi), mh = fminf(xh, cx - alo);
+    int ma = nx, mb = -1, pa = nx, pb = -1;
+    if (ml <= mh) {
+      ma = max((int)floorf(ml), 0);
+      mb = min((int)floorf(mh), nx - 1);
+    }
+    if (pl <= ph) {
+      pa = max((int)floorf(pl), 0);
+      pb = min((int)floorf(ph), nx - 1);
+    }
+    if (ma <= mb && pa <= pb && pa <= mb + 1) {  // touching or overlapping: one range
+      a0 = ma;
+      b0 = max(mb, pb);
+    } else if (ma <= mb) {
+      a0 = ma;
+      b0 = mb;
+      a1 = pa;
+      b1 = pb;
+    } else {
+      a0 = pa;
+      b0 = pb;
+    }
+  } else if (g.periodic) {
     if (hi - lo + 1 >= nx) {
       a0 = 0;
       b0 = nx - 1;
@@ -112,7 +152,8 @@ __device__ __forceinline__ void row_ranges(const StreamArgs& a, const Geom& g, c
   }
 }
 
-// GEN: bin edges not linear in r (the sphere's angle bins), count pass only
+// GEN: sphere mode -- bin edges not linear in r (the angle bins, count
+// pass) and rows cut to the points' shell (both passes)
 template <bool FILL, bool GEN>
 __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
   extern __shared__ uint32_t s_cnt_all[];
@@ -171,7 +212,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
 
     for (int t0 = 0, rb = 0; t0 < rw.nrows; t0 += 32, ++rb) {
       uint32_t s0, e0, s1, e1;
-      row_ranges(a, g, rw, t0 + lane, s0, e0, s1, e1);
+      row_ranges<GEN>(a, g, rw, t0 + lane, s0, e0, s1, e1);
       // this row block's range of the code buffer: its segments in the order
       // below, each padded to a multiple of 4 codes
       unsigned long long span = (s0 < e0 ? (e0 - s0 + 3u) & ~3u : 0u) + (s1 < e1 ? (e1 - s1 + 3u) & ~3u : 0u);
@@ -309,7 +350,7 @@ static size_t stream_smem(bool fill, int nbins) {
 }
 
 int stream_blocks_per_sm(bool fill, int nbins, bool general) {
-  const void* fn = fill ? (const void*)k_stream<true, false>
+  const void* fn = fill ? (general ? (const void*)k_stream<true, true> : (const void*)k_stream<true, false>)
                         : (general ? (const void*)k_stream<false, true> : (const void*)k_stream<false, false>);
   const size_t smem = stream_smem(fill, nbins);
   if (smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -320,19 +361,21 @@ int stream_blocks_per_sm(bool fill, int nbins, bool general) {
 
 cudaError_t launch_stream(const StreamArgs& a, bool fill, int nblocks, cudaStream_t st) {
   const size_t smem = stream_smem(fill, a.g.nbins);
-  if (fill) {
-    k_stream<true, false><<<nblocks, kStreamThreads, smem, st>>>(a);
-  } else {
-    const void* fn = a.g.general ? (const void*)k_stream<false, true> : (const void*)k_stream<false, false>;
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    if (a.g.general)
-      k_stream<false, true><<<nblocks, kStreamThreads, smem, st>>>(a);
-    else
-      k_stream<false, false><<<nblocks, kStreamThreads, smem, st>>>(a);
+  const bool gen = a.g.general != 0;
+  const void* fn = fill ? (gen ? (const void*)k_stream<true, true> : (const void*)k_stream<true, false>)
+                        : (gen ? (const void*)k_stream<false, true> : (const void*)k_stream<false, false>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
   }
+  if (fill && gen)
+    k_stream<true, true><<<nblocks, kStreamThreads, smem, st>>>(a);
+  else if (fill)
+    k_stream<true, false><<<nblocks, kStreamThreads, smem, st>>>(a);
+  else if (gen)
+    k_stream<false, true><<<nblocks, kStreamThreads, smem, st>>>(a);
+  else
+    k_stream<false, false><<<nblocks, kStreamThreads, smem, st>>>(a);
   ++g_launches;
   return cudaGetLastError();
 }

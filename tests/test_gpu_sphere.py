@@ -130,3 +130,17 @@ def test_sphere_mode_errors(ctbmod):
     with pytest.raises(ctbmod.CTBError) as e:
         est.edge_correct(z, z)
     assert e.value.code == ctbmod.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("cpr", [2, 6, 16])
+def test_points_off_the_unit_sphere(ctbmod, cpr):
+    """Directions scaled by 0.8-1.2: the rows are cut to the shell the points
+    occupy, and no pair may be lost at any grid size."""
+    xyz = synth.sphere_cap(5000, seed=89, theta_cap=0.3, centre=(0.3, 0.5, 0.81))
+    xyz = synth.snap_dyadic(xyz * np.random.default_rng(90).uniform(0.8, 1.2, (xyz.shape[0], 1)))
+    w = synth.sphere_field(xyz / np.linalg.norm(xyz, axis=1, keepdims=True), seed=91, width=0.04)
+    kw = dict(theta_min=0.002, theta_max=0.2, nbins=6, mmax=6)
+    z, est = run(ctbmod, xyz, w, kw, cells_per_rmax=cpr)
+    ref = oracle.zeta_sphere(xyz, w, **kw)
+    assert est.pair_count() == ref["npairs"]
+    assert zeta_err(z, ref) < TOL
