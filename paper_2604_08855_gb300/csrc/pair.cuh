@@ -9,9 +9,11 @@
 //
 // GB300 design.  The neighbour lists of a primary are grouped by bin
 // (stream.cu).  One warp owns one primary: for each of its (primary, bin)
-// lists each lane takes one neighbour per step, evaluates all (l, m)
+// lists each lane takes one neighbour per step, evaluates the (l, m)
 // coefficients of the direction by recurrences in float32 registers and
-// accumulates them (one FMA per coefficient).  At the end of the list the 32
+// accumulates them (one FMA per coefficient).  Up to l_max 10 one kernel
+// holds all coefficients; above, the m columns are split into passes of at
+// most 128 accumulators, each its own kernel and launch (see k_alm).  At the end of the list the 32
 // lanes' accumulators are summed through a shared-memory transpose, scaled by
 // the per-(l, m) normalisation and stored as the (primary, bin) row of M.
 // Each list is one run, so the cross-lane reduction happens once per

@@ -4,7 +4,9 @@
 // spatial index over the search range.  Here one warp owns one primary and
 // walks the x-rows of grid cells that intersect its ball r < r_max: each row
 // is one contiguous run of cell-sorted points, read with coalesced 16-byte
-// loads, 32 candidates per step.  Every candidate gets its exact radial bin:
+// loads, 32 candidates per step.  Rows are split finer along x than across
+// (kXSub), so a row's range ends close to the ball; in sphere mode a row is
+// also cut to the shell that holds the points.  Every candidate gets its exact radial bin:
 // float32 r from the fixed-point separation, and, for the rare candidates
 // within float rounding of an edge, the exact integer r^2 against exact
 // thresholds.
