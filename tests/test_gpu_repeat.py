@@ -82,3 +82,21 @@ def test_batch_repeat_bitwise(ctbmod):
     outs = three(ctbmod, make, lambda est: est.compute_batch(cats))
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+def test_shared_lists_repeat_bitwise(ctbmod):
+    xyz, w = synth.thomas(20000, 300.0, 200, 5.0, seed=94, weights="u0.5-1.5")
+
+    def make():
+        est = ctbmod.CTB(300.0, 2.0, 40.0, 8, 8)
+        est.set_points(xyz, w)
+        return est
+
+    def run(est):
+        return est.compute_shared(0.0), est.pair_sums(), est.pivot_groups()
+
+    outs = three(ctbmod, make, run)
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        assert np.array_equal(o[1], outs[0][1])
+        assert o[2] == outs[0][2]
