@@ -139,12 +139,14 @@ __global__ void __launch_bounds__(kConMaxThreads, 1) k_contract_fp32(ContractArg
     // coalesced loads of the rows (16 bytes when rows and base allow it),
     // scattered to [primary][coefficient][bin]
     if (vec4) {
+      // consecutive lanes take consecutive bins of the same four slots: their
+      // transposed stores land in consecutive words (no bank conflicts)
       const float4* src = reinterpret_cast<const float4*>(a.M + (uint64_t)pb * rowsz);
       const int row4 = a.row >> 2;
       for (int k = threadIdx.x; k < cnt * nb * row4; k += blockDim.x) {
-        const int pr = k / row4, c4 = k - pr * row4;  // pr = primary * nb + bin
-        const int q = pr / nb, b = pr - q * nb;
-        const float4 v = __ldcs(src + k);
+        const int r = k / nb, b = k - r * nb;  // r = primary * row4 + c4
+        const int q = r / row4, c4 = r - q * row4;
+        const float4 v = __ldcs(src + ((q * nb + b) * row4 + c4));
         const float e[4] = {v.x, v.y, v.z, v.w};
         float* dst = s_rows + q * per + b;
 #pragma unroll
