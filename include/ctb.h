@@ -186,8 +186,10 @@ int ctb_compute_subset(ctb_ctx* ctx, const int64_t* primary_idx, int64_t m, doub
  *               of them and from either.  The angular term follows from
  *               Bernstein's inequality, |d/dgamma P_l(cos gamma)| <= l.  This
  *               is a statement about the estimate, up to FP32 rounding of the
- *               computation, for the 3-D multipoles; no bound is stated for
- *               the sphere mode's projected multipoles.
+ *               computation.  Sphere mode: the same sum with m for l and,
+ *               for the angle, the angle between p's tangent direction to j
+ *               and c's carried to p's tangent plane by the rotation taking
+ *               c's normal to p's (|d/dpsi cos(m psi)| <= m).
  *   pivot_cell  h > 0, or 0 for the mean separation: (V / n)^(1/3) with
  *               V = box^3 (periodic) or the product of the bounding box's
  *               sides, each at least r_max (open); sqrt(4 pi / n) on the

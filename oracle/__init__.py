@@ -17,8 +17,8 @@ Parity status of each function (what pins it is listed in the tests):
          projections), the m = 0 closed form with scipy's cKDTree chord
          counts, a hand geometry at the pole and on the equator, rotation
          invariance.
-  shared.*  the shared-neighbour-list estimate and its error bound; the
-         pins are listed in shared.py.
+  shared.*  the shared-neighbour-list estimate and its error bounds (3-D
+         and sphere); the pins are listed in shared.py.
   edge.edge_correct  pinned: sympy's Wigner 3j symbols, exact Legendre
          quotients built with numpy's legmul, flat randoms (plain ratio),
          quadrature of N/R.

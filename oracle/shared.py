@@ -54,7 +54,20 @@ Parity status (what pins each function is in tests/test_oracle_shared.py):
                   groups, and linear in the displacement where no
                   membership changes.
   zeta_shared_sphere  pinned: equals oracle.zeta_sphere for singleton groups
-                  and coincident pairs.
+                  and coincident pairs; lies within shared_bound_sphere of it.
+  shared_bound_sphere  pinned: an O(N^3) triplet sum of |term differences|,
+                  with each pivot's angles taken from its own tangent frame,
+                  lies between |dzeta| and the bound; zero for singleton and
+                  coincident groups.
+
+Sphere bound.  zeta_m = sum_p w_p sum_{j,k} w_j w_k cos(m psi_p(j,k)), psi_p
+the signed angle between the tangent-plane projections at p of n_j - n_p
+and n_k - n_p.  The rotation R that takes c's normal to p's maps c's tangent
+plane onto p's and keeps signed angles.  So psi_c - psi_p is at most
+beta_j + beta_k (mod 2 pi), beta_j being the angle between p's projection
+of j and R applied to c's.  |d/dpsi cos(m psi)| <= m, so the same sum as in
+3-D holds, with beta for alpha and m for l (beta = pi where a projection
+vanishes).
 """
 from __future__ import annotations
 
@@ -196,6 +209,96 @@ def shared_bound(xyz, w, box, rmin, rmax, nbins, lmax, h):
             D[b] = aw[ip ^ ic].sum()
             U[b] = aw[ip | ic].sum()
         ang = np.minimum(ells * (np.outer(A, S) + np.outer(S, A))[None], 2.0 * np.outer(S, S)[None])
+        mem = np.outer(D, U) + np.outer(U, D)
+        B += aw[p] * (ang + mem[None])
+    return B
+
+
+def _sphere_edges(theta_min, theta_max, nbins):
+    """Chord edges 2 sin(theta_b / 2), computed as oracle.zeta_sphere does (libm sin)."""
+    import math
+    return np.array([2.0 * math.sin(0.5 * (theta_min + b * (theta_max - theta_min) / nbins))
+                     for b in range(nbins + 1)])
+
+
+def _sphere_bins(xyz, i, edges):
+    """Bin of every chord from point i as oracle.zeta_sphere decides it (-1: none)."""
+    d = xyz - xyz[i]
+    c = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2])
+    ok = (c > 0.0) & (c >= edges[0]) & (c < edges[-1])
+    ok[i] = False
+    b = np.searchsorted(edges, c, side="right") - 1
+    return np.where(ok, b, -1)
+
+
+def _tangent_dirs(xyz, i):
+    """Unit tangent-plane directions at point i of x_j - x_i, and where they exist."""
+    n = xyz[i] / np.linalg.norm(xyz[i])
+    d = xyz - xyz[i]
+    t = d - np.outer(d @ n, n)
+    nt = np.linalg.norm(t, axis=1)
+    ok = nt > 0.0
+    t[ok] /= nt[ok, None]
+    return t, ok
+
+
+def _rotation(a, b):
+    """Rotation taking the unit vector a to the unit vector b (about a x b)."""
+    v = np.cross(a, b)
+    s = np.linalg.norm(v)
+    c = float(a @ b)
+    if s == 0.0:
+        if c > 0.0:
+            return np.eye(3)
+        p = np.array([1.0, 0.0, 0.0]) if abs(a[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+        k = np.cross(a, p)
+        k /= np.linalg.norm(k)
+        return 2.0 * np.outer(k, k) - np.eye(3)  # half turn about k, which is orthogonal to a
+    k = v / s
+    K = np.array([[0.0, -k[2], k[1]], [k[2], 0.0, -k[0]], [-k[1], k[0], 0.0]])
+    return np.eye(3) + s * K + (1.0 - c) * (K @ K)
+
+
+def shared_bound_sphere(xyz, w, theta_min, theta_max, nbins, mmax, h):
+    """Entrywise bound [mmax+1][nbins][nbins] on |zeta_shared_sphere -
+    zeta_sphere| (module docstring), by brute force over every member and
+    every neighbour."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    ww = np.ones(n) if w is None else np.asarray(w, dtype=np.float64)
+    aw = np.abs(ww)
+    label, rep, _ = _groups(xyz, ww, float(h), 0.0)
+    edges = _sphere_edges(theta_min, theta_max, nbins)
+    ms = np.arange(mmax + 1, dtype=np.float64)[:, None, None]
+    B = np.zeros((mmax + 1, nbins, nbins))
+    for p in range(n):
+        c = int(rep[label[p]])
+        if c == p:
+            continue
+        bp = _sphere_bins(xyz, p, edges)
+        bc = _sphere_bins(xyz, c, edges)
+        same = (bp == bc) & (bp >= 0)
+        tp, okp = _tangent_dirs(xyz, p)
+        tc, okc = _tangent_dirs(xyz, c)
+        R = _rotation(xyz[c] / np.linalg.norm(xyz[c]), xyz[p] / np.linalg.norm(xyz[p]))
+        tcr = tc @ R.T
+        beta = np.full(n, np.pi)
+        good = same & okp & okc
+        cr = np.cross(tp[good], tcr[good])
+        beta[good] = np.arctan2(np.sqrt(np.sum(cr * cr, axis=1)), np.sum(tp[good] * tcr[good], axis=1))
+        S = np.zeros(nbins)
+        A = np.zeros(nbins)
+        D = np.zeros(nbins)
+        U = np.zeros(nbins)
+        for b in range(nbins):
+            ip = bp == b
+            ic = bc == b
+            both = ip & ic
+            S[b] = aw[both].sum()
+            A[b] = (aw[both] * beta[both]).sum()
+            D[b] = aw[ip ^ ic].sum()
+            U[b] = aw[ip | ic].sum()
+        ang = np.minimum(ms * (np.outer(A, S) + np.outer(S, A))[None], 2.0 * np.outer(S, S)[None])
         mem = np.outer(D, U) + np.outer(U, D)
         B += aw[p] * (ang + mem[None])
     return B

@@ -5,7 +5,8 @@
 - the stated bound: |shared - exact oracle| <= shared_bound + 1e-5 x scale;
 - one-point groups reproduce the exact oracle; the automatic cell side is
   the mean separation;
-- the sphere mode, the shared 2PCF, and the argument errors.
+- the sphere mode (parity with the oracle's shared estimate, and the sphere
+  bound against the exact oracle), the shared 2PCF, and the argument errors.
 """
 import numpy as np
 import pytest
@@ -138,6 +139,24 @@ def test_shared_sphere_vs_oracle(ctbmod):
     assert g < xyz.shape[0]
     assert est.pair_count() == ref["npairs"]
     assert zeta_err(z, ref) < TOL
+
+
+def test_shared_sphere_within_stated_bound(ctbmod):
+    """The projected multipoles: GPU shared estimate vs the exact oracle,
+    within the sphere bound of oracle/shared.py."""
+    xyz = synth.snap_dyadic(synth.sphere_cap(3000, seed=609, theta_cap=0.25, centre=(0.2, 0.4, 0.89)))
+    w = synth.sphere_field(xyz / np.linalg.norm(xyz, axis=1, keepdims=True), seed=610, width=0.04)
+    kw = dict(theta_min=0.005, theta_max=0.15, nbins=5, mmax=8)
+    h = 0.02
+    est = ctbmod.CTB.sphere(kw["theta_min"], kw["theta_max"], kw["nbins"], kw["mmax"])
+    est.set_points(xyz, w)
+    z = est.compute_shared(h)
+    assert est.pivot_groups()[1] < xyz.shape[0]
+    exact = oracle.zeta_sphere(xyz, w, **kw)
+    B = shared.shared_bound_sphere(xyz, w, h=h, **kw)
+    dev = np.abs(z - exact["zeta"])
+    assert np.all(dev <= B + TOL * gram_scale(exact))
+    assert np.any(dev > 10 * TOL * gram_scale(exact))
 
 
 def test_shared_errors(ctbmod):

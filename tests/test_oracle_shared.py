@@ -230,3 +230,139 @@ def test_bound_hand_geometry():
     aj = np.arctan(0.1 / 3.0)
     for l in range(5):
         np.testing.assert_allclose(B[l], 2.0 * np.array([[18 * l * aj + 80, 65], [65, 50]]), rtol=1e-13)
+
+
+def _cap(n, seed, theta=0.25, centre=(0.3, -0.2, 0.93)):
+    rng = np.random.default_rng(seed)
+    c = np.asarray(centre, float)
+    c /= np.linalg.norm(c)
+    mu = rng.uniform(np.cos(theta), 1.0, n)
+    ph = rng.uniform(0.0, 2 * np.pi, n)
+    s = np.sqrt(1 - mu * mu)
+    local = np.stack([s * np.cos(ph), s * np.sin(ph), mu], axis=1)
+    z = np.array([0.0, 0.0, 1.0])
+    v = np.cross(z, c)
+    sn, cs = np.linalg.norm(v), z @ c
+    k = v / sn
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return synth.snap_dyadic(local @ (np.eye(3) + sn * K + (1 - cs) * K @ K).T)
+
+
+def test_sphere_bound_zero_for_singletons_and_coincident_groups():
+    xyz = _cap(300, 510)
+    w = np.random.default_rng(511).uniform(-1.0, 1.0, 300)
+    kw = dict(theta_min=0.01, theta_max=0.3, nbins=4, mmax=5)
+    assert not np.any(shared.shared_bound_sphere(xyz, w, h=1e-5, **kw))
+    xyz2 = np.concatenate([xyz, xyz])
+    w2 = np.concatenate([w, 1.0 - w])
+    assert shared.pivot_groups(xyz2, 1e-5)[1].shape[0] == 300
+    assert not np.any(shared.shared_bound_sphere(xyz2, w2, h=1e-5, **kw))
+
+
+def _sphere_triplet_difference(xyz, w, theta_min, theta_max, nbins, mmax, rep_of):
+    """sum_p w_p sum_{j,k} w_j w_k (T_c - T_p) and its absolute version; T_x =
+    cos(m (phi_xj - phi_xk)) [bins], phi in a tangent frame built here."""
+    import math
+    n = xyz.shape[0]
+    edges = np.array([2.0 * math.sin(0.5 * (theta_min + b * (theta_max - theta_min) / nbins))
+                      for b in range(nbins + 1)])
+
+    def view(x):
+        nx = xyz[x] / np.linalg.norm(xyz[x])
+        e1 = np.cross(nx, [0.3, 0.5, 0.8])
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(nx, e1)
+        d = xyz - xyz[x]
+        chord = np.linalg.norm(d, axis=1)
+        b = np.full(n, -1)
+        ok = (chord > 0) & (chord >= edges[0]) & (chord < edges[-1])
+        b[ok] = np.searchsorted(edges, chord[ok], side="right") - 1
+        b[x] = -1
+        u, v = d @ e1, d @ e2
+        phi = np.where((u == 0) & (v == 0), 0.0, np.arctan2(v, u))
+        C = np.stack([np.cos(m * (phi[:, None] - phi[None, :])) for m in range(mmax + 1)])
+        ind = np.stack([b == k for k in range(nbins)]).astype(float)
+        return C, ind
+
+    sig = np.zeros((mmax + 1, nbins, nbins))
+    ab = np.zeros_like(sig)
+    ww = np.outer(w, w)[None]
+    for p in range(n):
+        c = rep_of[p]
+        if c == p:
+            continue
+        Cp, Ip = view(p)
+        Cc, Ic = view(c)
+        for b1 in range(nbins):
+            for b2 in range(nbins):
+                Tp = Cp * np.outer(Ip[b1], Ip[b2])[None]
+                Tc = Cc * np.outer(Ic[b1], Ic[b2])[None]
+                sig[:, b1, b2] += w[p] * np.sum(ww * (Tc - Tp), axis=(1, 2))
+                ab[:, b1, b2] += abs(w[p]) * np.sum(np.abs(ww) * np.abs(Tc - Tp), axis=(1, 2))
+    return sig, ab
+
+
+def test_sphere_bound_against_triplet_sum():
+    xyz = _cap(45, 512, theta=0.2)
+    w = np.random.default_rng(513).uniform(-0.5, 1.5, 45)
+    kw = dict(theta_min=0.01, theta_max=0.2, nbins=3, mmax=4)
+    h = 0.05
+    label, rep, _ = shared.pivot_groups(xyz, h)
+    assert rep.shape[0] < 40
+    sig, ab = _sphere_triplet_difference(xyz, w, rep_of=rep[label], **kw)
+    s = shared.zeta_shared_sphere(xyz, w, h=h, **kw)
+    e = oracle.zeta_sphere(xyz, w, **kw)
+    dz = s["zeta"] - e["zeta"]
+    scale = np.abs(e["zeta"]).max()
+    np.testing.assert_allclose(dz, sig, rtol=1e-9, atol=1e-11 * scale)
+    B = shared.shared_bound_sphere(xyz, w, h=h, **kw)
+    assert np.all(np.abs(dz) <= ab + 1e-11 * scale)
+    assert np.all(ab <= B + 1e-11 * scale)
+    assert np.any(np.abs(dz) > 1e-6 * scale)
+
+
+@pytest.mark.parametrize("h", [0.01, 0.03])
+def test_sphere_bound_holds_on_a_field(h):
+    xyz = _cap(900, 514, theta=0.3)
+    w = synth.sphere_field(xyz / np.linalg.norm(xyz, axis=1, keepdims=True), seed=515, width=0.05)
+    kw = dict(theta_min=0.005, theta_max=0.15, nbins=4, mmax=6)
+    s = shared.zeta_shared_sphere(xyz, w, h=h, **kw)
+    e = oracle.zeta_sphere(xyz, w, **kw)
+    B = shared.shared_bound_sphere(xyz, w, h=h, **kw)
+    dz = np.abs(s["zeta"] - e["zeta"])
+    scale = np.abs(e["zeta"]).max()
+    assert np.all(dz <= B + 1e-10 * scale)
+    assert np.any(dz > 1e-8 * scale)
+
+
+def test_sphere_bound_hand_geometry():
+    # c at the pole and p = delta along the meridian phi = 0 share a cell.
+    # j is at colatitude theta on the meridian phi = 90 deg.  In the right
+    # spherical triangle (c, p, j) Napier's rule gives tan A = tan(theta) /
+    # sin(delta) at p, so the transported direction (east) and p's direction
+    # to j differ by beta_j = atan(sin(delta) / tan(theta)).  k lies on the
+    # great circle through c and p, so beta_k = 0.  Bins [0.05, 0.15) and
+    # [0.15, 0.25) hold j and k from both; w = (1, 2, 3, 5), so S = (3, 5),
+    # A = (3 beta_j, 0), D = 0, and only p (|w_p| = 2) contributes.
+    delta, theta, theta_k = 0.01, 0.1, 0.2
+    pts = np.array([
+        [0.0, 0.0, 1.0],
+        [np.sin(delta), 0.0, np.cos(delta)],
+        [0.0, np.sin(theta), np.cos(theta)],
+        [-np.sin(theta_k), 0.0, np.cos(theta_k)],
+    ])
+    # the whole configuration rotated a little, so that c is off the cell faces
+    g = 0.3
+    R = np.array([[np.cos(g), 0.0, np.sin(g)], [0.0, 1.0, 0.0], [-np.sin(g), 0.0, np.cos(g)]])
+    xyz = pts @ R.T
+    w = np.array([1.0, 2.0, 3.0, 5.0])
+    h = 0.04
+    label, rep, _ = shared.pivot_groups(xyz, h)
+    assert label[0] == label[1] and len({label[0], label[2], label[3]}) == 3
+    kw = dict(theta_min=0.05, theta_max=0.25, nbins=2, mmax=4)
+    B = shared.shared_bound_sphere(xyz, w, h=h, **kw)
+    bj = np.arctan(np.sin(delta) / np.tan(theta))
+    for m in range(5):
+        want = 2.0 * np.array([[min(m * 18 * bj, 18.0), min(m * 15 * bj, 30.0)],
+                               [min(m * 15 * bj, 30.0), 0.0]])
+        np.testing.assert_allclose(B[m], want, rtol=1e-9, atol=1e-12)
