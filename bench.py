@@ -44,7 +44,7 @@ INST_PER_UPDATE = 2.6
 # DRAM bytes per pair of the accumulation kernel from one ncu capture of the
 # current k_alm (dram__bytes_read.sum + dram__bytes_write.sum over the pairs of
 # the captured launch); None when the kernel changed after the capture.
-K_ALM_DRAM_BYTES_PER_PAIR = 4.347
+K_ALM_DRAM_BYTES_PER_PAIR = 4.395
 FP32_LANES_PER_SM = 128
 
 
