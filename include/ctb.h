@@ -335,8 +335,8 @@ int ctb_get_grid(ctb_ctx* ctx, int* cells_per_rmax, int* cells_per_axis);
  * hand out only fixed buffers, or loops with a latency budget in which an
  * allocation, or its failure, is not acceptable.  It runs the same FP32
  * contraction and FP64 normalisation as ctb_compute, with its per-block
- * partial sums in a fixed, file-scope device array of the library (8 MB on
- * every GPU that loads the library, held until the process exits).
+ * partial sums in a fixed, file-scope device array of the library: 8 MB on
+ * every GPU that loads the library, held until the process exits.
  *   alm       [np][nbins][(ell_max+1)^2] float32, device; coefficient (l, m)
  *             at index l*l + l + m (the layout of ctb_get_alm)
  *   w         [np] float32 primary weights, device
@@ -345,14 +345,18 @@ int ctb_get_grid(ctb_ctx* ctx, int* cells_per_rmax, int* cells_per_axis);
  *   stream    cudaStream_t to run on (NULL = legacy default); the call returns
  *             once the work is queued
  * Limits: nbins 1..CTB_NBINS_CAP, ell_max 0..CTB_LMAX_CAP and
- * (ell_max+1) * nbins^2 <= 16384 (the size of the fixed array); otherwise
- * CTB_ERR_ARG.  A failed CUDA call gives CTB_ERR_CUDA.  ctb_last_error()
- * does not describe failures of this call.
- * The first call on a device looks up the array's device address (with that
- * device current) and initialises a small table on the given stream; make
- * that first call before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU race and must be serialised by the
- * caller (e.g. one stream).  Each call clears the part it uses first.
+ * (ell_max+1) * nbins^2 <= 16384 (the array then holds at least 64 partial
+ * blocks); otherwise CTB_ERR_ARG.  A failed CUDA call gives CTB_ERR_CUDA.
+ * ctb_last_error() does not describe failures of this call.
+ * The first call on a device looks up the array's device address and the SM
+ * count with that device current (no device work); make that first call
+ * before any stream capture.  The partials use one wave of the contraction's
+ * resident blocks, as far as the array holds them.  All calls share the
+ * array: calls whose work overlaps on the GPU race and must be serialised by
+ * the caller (e.g. one stream).  Each call first clears the partial blocks it
+ * uses (nparts * (ell_max+1) * nbins^2 values), and its finalisation reads
+ * exactly those, so what an earlier call with another shape left beyond them
+ * is never read.
  */
 int ctb_contract_noalloc(const float* alm, const float* w, int64_t np, int nbins, int ell_max,
                          double* zeta_out, void* stream);

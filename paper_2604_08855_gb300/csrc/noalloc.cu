@@ -14,30 +14,37 @@
 // overlap on the GPU race on it).  Host code must not use the array's name as
 // a device address: the device address is taken with cudaGetSymbolAddress,
 // once per device, with that device current, on the first call.
+#include <algorithm>
 #include <mutex>
 
 #include "ctb_internal.cuh"
 
 namespace ctb {
 
-constexpr int kNoallocParts = 64;                   // contraction blocks (partial rows)
+constexpr int kNoallocMinParts = 64;                // partial rows the size limit guarantees
 constexpr size_t kNoallocPartialDoubles = 1 << 20;  // 8 MB of FP64 partials
 constexpr int kNoallocMaxDevices = 64;
 
-// partial[part][l][b1][b2]; cleared at the start of every call
+// partial[part][l][b1][b2]; the part a call uses is cleared at its start
 static __device__ __align__(256) double g_noalloc_partial[kNoallocPartialDoubles];
-// identity slot table for rows in the l*l + l + m order (written at set-up)
-static __device__ __align__(256) int g_noalloc_slot[(kLmaxCap + 1) * (kLmaxCap + 1)];
 
-static __global__ void k_noalloc_identity(int* slot, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) slot[i] = i;
-}
+// Identity slot table for rows in the l*l + l + m order.  It is constant-
+// initialised in the module image, so no set-up kernel has to write it before
+// the first contraction can read it.
+struct IdentitySlots {
+  int v[(kLmaxCap + 1) * (kLmaxCap + 1)];
+  constexpr IdentitySlots() : v() {
+    for (int i = 0; i < (kLmaxCap + 1) * (kLmaxCap + 1); ++i) v[i] = i;
+  }
+};
+static __device__ __align__(256) IdentitySlots g_noalloc_slot = IdentitySlots();
 
 namespace {
 struct DevScratch {
   bool ready = false;
   double* partial = nullptr;
   int* slot = nullptr;
+  int nsm = 0;
 };
 std::mutex g_noalloc_mu;
 DevScratch g_noalloc_dev[kNoallocMaxDevices];
@@ -53,8 +60,9 @@ extern "C" int ctb_contract_noalloc(const float* alm, const float* w, int64_t np
   if (np < 0) return CTB_ERR_ARG;
   if (!zeta_out || (np > 0 && (!alm || !w))) return CTB_ERR_ARG;
   const size_t per_part = (size_t)(ell_max + 1) * nbins * nbins;
-  // (ell_max + 1) * nbins^2 must not exceed 16384: the fixed scratch holds 64 such blocks
-  if (per_part * kNoallocParts > kNoallocPartialDoubles) return CTB_ERR_ARG;
+  // (ell_max + 1) * nbins^2 must not exceed 16384: the fixed scratch holds at
+  // least 64 partial blocks of that size
+  if (per_part * kNoallocMinParts > kNoallocPartialDoubles) return CTB_ERR_ARG;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return CTB_ERR_CUDA;
@@ -65,7 +73,8 @@ extern "C" int ctb_contract_noalloc(const float* alm, const float* w, int64_t np
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     DevScratch& d = g_noalloc_dev[dev];
     if (!d.ready) {
-      // set-up, once per device, with this device current
+      // set-up, once per device, with this device current: the device
+      // addresses of the file-scope arrays and the SM count (no device work)
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_partial);
       if (e != cudaSuccess) return CTB_ERR_CUDA;
@@ -73,16 +82,22 @@ extern "C" int ctb_contract_noalloc(const float* alm, const float* w, int64_t np
       e = cudaGetSymbolAddress(&p, g_noalloc_slot);
       if (e != cudaSuccess) return CTB_ERR_CUDA;
       d.slot = static_cast<int*>(p);
-      k_noalloc_identity<<<1, 256, 0, st>>>(d.slot, (kLmaxCap + 1) * (kLmaxCap + 1));
-      ++g_launches;
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return CTB_ERR_CUDA;
+      e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess || d.nsm < 1) return CTB_ERR_CUDA;
       d.ready = true;
     }
     sc = d;
   }
+  // One partial row per contraction block: one wave of the kernel's resident
+  // blocks (as ctb_compute runs it), as far as the fixed array holds them, so
+  // that each block's FP32 run over its slice of the primaries stays short.
+  const int row = (ell_max + 1) * (ell_max + 1);
+  const int bps = contract_fp32_blocks_per_sm(nbins, ell_max, row, 0);
+  if (bps < 1) return CTB_ERR_CUDA;
+  const int nparts = (int)std::min<size_t>((size_t)bps * sc.nsm, kNoallocPartialDoubles / per_part);
   // the partial sums are accumulated in place: clear the part this call uses
-  e = cudaMemsetAsync(sc.partial, 0, per_part * kNoallocParts * sizeof(double), st);
+  // (the finalisation reads exactly these nparts * per_part entries)
+  e = cudaMemsetAsync(sc.partial, 0, per_part * nparts * sizeof(double), st);
   if (e != cudaSuccess) return CTB_ERR_CUDA;
   if (np > 0) {
     ContractArgs ca{};
@@ -91,14 +106,14 @@ extern "C" int ctb_contract_noalloc(const float* alm, const float* w, int64_t np
     ca.np = np;
     ca.nbins = nbins;
     ca.lmax = ell_max;
-    ca.row = (ell_max + 1) * (ell_max + 1);
+    ca.row = row;
     ca.slot = sc.slot;
     ca.partial = sc.partial;
     ca.part0 = 0;
-    e = launch_contract_fp32(ca, kNoallocParts, st);
+    e = launch_contract_fp32(ca, nparts, st);
     if (e != cudaSuccess) return CTB_ERR_CUDA;
   }
-  e = launch_finalize(sc.partial, kNoallocParts, ell_max, nbins, zeta_out, false, st);
+  e = launch_finalize(sc.partial, nparts, ell_max, nbins, zeta_out, false, st);
   if (e != cudaSuccess) return CTB_ERR_CUDA;
   return CTB_OK;
 }

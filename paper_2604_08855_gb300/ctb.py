@@ -317,10 +317,29 @@ class CTB:
 
 def contract_noalloc(alm, w, nbins: int, lmax: int, out, stream=None) -> None:
     """zeta from device a_lm rows [np][nbins][(lmax+1)^2] and device weights [np]
-    (float32 CUDA tensors) into `out` (float64 CUDA tensor), with no device
-    allocation by the library; see ctb_contract_noalloc in include/ctb.h."""
+    (float32 CUDA tensors) into `out` (float64 CUDA tensor [(lmax+1), nbins,
+    nbins]), with no device allocation by the library; see
+    ctb_contract_noalloc in include/ctb.h.  `stream` defaults to torch's
+    current stream on the tensors' device."""
+    import torch
     lib = load()
-    if stream is not None and hasattr(stream, "cuda_stream"):
+    nc = (int(lmax) + 1) ** 2
+    checks = (
+        (all(isinstance(t, torch.Tensor) and t.is_cuda for t in (alm, w, out)), "alm, w and out must be CUDA tensors"),
+        (alm.device == w.device == out.device, "alm, w and out must be on one device"),
+        (alm.dtype == torch.float32 and w.dtype == torch.float32, "alm and w must be float32"),
+        (out.dtype == torch.float64, "out must be float64"),
+        (alm.is_contiguous() and w.is_contiguous() and out.is_contiguous(), "alm, w and out must be contiguous"),
+        (alm.dim() == 3 and tuple(alm.shape[1:]) == (int(nbins), nc), f"alm must be [np][{nbins}][{nc}]"),
+        (w.dim() == 1 and w.shape[0] == alm.shape[0], "w needs one weight per primary"),
+        (tuple(out.shape) == (int(lmax) + 1, int(nbins), int(nbins)), f"out must be [{lmax + 1}][{nbins}][{nbins}]"),
+    ) if isinstance(alm, torch.Tensor) else ((False, "alm, w and out must be CUDA tensors"),)
+    for ok, msg in checks:
+        if not ok:
+            raise ValueError(msg)
+    if stream is None:
+        stream = torch.cuda.current_stream(alm.device)
+    if hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     np_ = int(alm.shape[0])
     rc = lib.ctb_contract_noalloc(_ptr(alm), _ptr(w), np_, int(nbins), int(lmax), _ptr(out),
