@@ -13,6 +13,11 @@ Parity status of each function (what pins it is listed in the tests):
   zeta   pinned: O(N^3) triplet sum with numpy Legendre polynomials, the
          l = 0 closed form with scipy's cKDTree neighbour counts, hand-built
          geometries with printed P_l values, invariances.
+  contract  the contraction of given a_lm rows alone; pinned: it reproduces
+         zeta from the oracle's own a_lm (whose zeta is pinned as above).
+  ambiguous  the pairs within a relative tolerance of a bin edge; pinned:
+         hand-placed pairs at and near edges, and its count equals zeta's
+         namb.
   zeta_sphere  pinned: frame-free triplet sum (angles between tangent
          projections), the m = 0 closed form with scipy's cKDTree chord
          counts, a hand geometry at the pole and on the equator, rotation
@@ -23,5 +28,5 @@ Parity status of each function (what pins it is listed in the tests):
          quotients built with numpy's legmul, flat randoms (plain ratio),
          quadrature of N/R.
 """
-from .oracle import build, ylm, alm, zeta, zeta_sphere, max_threads, lib_path  # noqa: F401
+from .oracle import build, ylm, alm, ambiguous, contract, zeta, zeta_sphere, max_threads, lib_path  # noqa: F401
 from . import edge, shared  # noqa: F401

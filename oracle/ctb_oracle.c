@@ -304,6 +304,54 @@ int oracle_zeta(const double* xyz, const double* w, int64_t n, double box, doubl
     return 0;
 }
 
+/*
+ * Edge-ambiguous pairs of the listed primaries: every (p, j) whose separation
+ * r lies within amb_tol * r of an edge rmin + k D, k = 0..nbins (so within the
+ * rounding of any binning that is not exact in FP64 -- e.g. one that first
+ * rounds the coordinates onto a fixed-point grid -- it may land on the other
+ * side of that edge).  Up to `cap` records are written, in primary order:
+ *   rec_i[2 t]     index of the primary in the list (i, not p)
+ *   rec_i[2 t + 1] j
+ *   rec_d[5 t..]   separation vector d (3), r, and the edge index k
+ * Returns the number of such pairs (which may exceed cap), or -1 on bad
+ * arguments.  Serial: the record order is fixed.
+ */
+int64_t oracle_ambiguous(const double* xyz, int64_t n, double box, double rmin, double rmax, int nbins,
+                         const int64_t* prim, int64_t np, double amb_tol, int64_t* rec_i, double* rec_d,
+                         int64_t cap)
+{
+    if (check_args(n, box, rmin, rmax, nbins, 0) || !(amb_tol > 0.0)) return -1;
+    if (!prim) np = n;
+    const double dr = (rmax - rmin) / nbins;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < np; ++i) {
+        int64_t p = prim ? prim[i] : i;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == p) continue;
+            double d[3];
+            separation(xyz, p, j, box, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (r == 0.0) continue;
+            for (int k = 0; k <= nbins; ++k) {
+                if (fabs(r - (rmin + k * dr)) < amb_tol * r) {
+                    if (cnt < cap) {
+                        rec_i[2 * cnt] = i;
+                        rec_i[2 * cnt + 1] = j;
+                        rec_d[5 * cnt] = d[0];
+                        rec_d[5 * cnt + 1] = d[1];
+                        rec_d[5 * cnt + 2] = d[2];
+                        rec_d[5 * cnt + 3] = r;
+                        rec_d[5 * cnt + 4] = (double)k;
+                    }
+                    ++cnt;
+                    break;
+                }
+            }
+        }
+    }
+    return cnt;
+}
+
 /* Number of OpenMP threads a parallel region gets (1 without OpenMP). */
 int oracle_max_threads(void)
 {

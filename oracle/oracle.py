@@ -54,6 +54,8 @@ def _load():
         lib.oracle_zeta.restype = i32
         lib.oracle_zeta_sphere.argtypes = [vp, vp, i64, d, d, i32, i32, vp, i64, vp, vp, vp, vp, i32, vp]
         lib.oracle_zeta_sphere.restype = i32
+        lib.oracle_ambiguous.argtypes = [vp, i64, d, d, d, i32, vp, i64, d, vp, vp, i64]
+        lib.oracle_ambiguous.restype = i64
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = i32
         _lib = lib
@@ -114,6 +116,45 @@ def alm(xyz, w, box, rmin, rmax, nbins, lmax, prim=None, nthreads=0):
     if rc != 0:
         raise ValueError(f"oracle_alm rejected its arguments (rc={rc})")
     return out
+
+
+def ambiguous(xyz, box, rmin, rmax, nbins, amb_tol, prim=None, cap=4096):
+    """Pairs (i, j) -- i the index into ``prim`` (or the primary itself) --
+    whose separation lies within amb_tol * r of a bin edge rmin + k D
+    (k = 0..nbins), where a binning that is not exact in FP64 may disagree
+    with this oracle's.  Returns (idx [m][2] int64, d [m][3], r [m],
+    edge [m] int); raises if more than ``cap`` pairs qualify."""
+    lib = _load()
+    xyz, _ = _points(xyz, None)
+    prim = _prim(prim)
+    n = xyz.shape[0]
+    np_ = n if prim is None else prim.shape[0]
+    ri = np.zeros((cap, 2), dtype=np.int64)
+    rd = np.zeros((cap, 5))
+    m = lib.oracle_ambiguous(_ptr(xyz), n, float(box), float(rmin), float(rmax), int(nbins), _ptr(prim), np_,
+                             float(amb_tol), _ptr(ri), _ptr(rd), cap)
+    if m < 0:
+        raise ValueError("oracle_ambiguous rejected its arguments")
+    if m > cap:
+        raise ValueError(f"{m} ambiguous pairs, more than cap = {cap}")
+    return ri[:m], rd[:m, :3], rd[:m, 3], rd[:m, 4].astype(int)
+
+
+def contract(alm_rows, wprim, lmax):
+    """zeta_l(b1, b2) = 4 pi / (2l+1) sum_p w_p sum_{m=-l..l} a_lm(p, b1) a_lm(p, b2)
+    from given a_lm rows [np][nbins][(lmax+1)^2] (index l*l + l + m) and
+    primary weights [np], in float64: the contraction step of the estimator
+    definition alone (the same formula ``zeta`` applies to its own a_lm)."""
+    a = np.asarray(alm_rows, dtype=np.float64)
+    wp = np.asarray(wprim, dtype=np.float64)
+    if a.ndim != 3 or a.shape[2] != (lmax + 1) ** 2 or wp.shape != (a.shape[0],):
+        raise ValueError("alm_rows must be [np][nbins][(lmax+1)^2] and wprim [np]")
+    nb = a.shape[1]
+    z = np.zeros((lmax + 1, nb, nb))
+    for l in range(lmax + 1):
+        sl = a[:, :, l * l:(l + 1) * (l + 1)]          # [np][nbins][2l+1]
+        z[l] = 4.0 * np.pi / (2 * l + 1) * np.einsum("p,pim,pjm->ij", wp, sl, sl)
+    return z
 
 
 def _wprim(wprim, np_):

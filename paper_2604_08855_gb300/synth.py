@@ -47,20 +47,24 @@ def snap_dyadic(xyz, step: float = 2.0 ** -20):
 # primitive generators
 
 
-def uniform(n: int, box: float, seed: int, weights: str = "unit"):
+def uniform(n: int, box: float, seed: int, weights: str = "unit", snap: bool = True):
+    """N uniform points in a periodic cube; snap=False keeps the raw float64
+    draws (off the fixed-point grid)."""
     rng = np.random.default_rng(seed)
-    xyz = snap_periodic(rng.uniform(0.0, box, size=(n, 3)), box)
+    xyz = rng.uniform(0.0, box, size=(n, 3))
+    xyz = snap_periodic(xyz, box) if snap else xyz
     w = _weights(rng, n, weights)
     return xyz, w
 
 
-def thomas(n: int, box: float, n_par: int, sigma: float, seed: int, weights: str = "unit"):
-    """Thomas process in a periodic cube, exactly n points."""
+def thomas(n: int, box: float, n_par: int, sigma: float, seed: int, weights: str = "unit", snap: bool = True):
+    """Thomas process in a periodic cube, exactly n points; snap=False keeps
+    the raw float64 values wrapped into [0, box) (off the fixed-point grid)."""
     rng = np.random.default_rng(seed)
     parents = rng.uniform(0.0, box, size=(n_par, 3))
     owner = rng.integers(0, n_par, size=n)
     xyz = parents[owner] + rng.normal(0.0, sigma, size=(n, 3))
-    xyz = snap_periodic(xyz, box)
+    xyz = snap_periodic(xyz, box) if snap else np.mod(xyz, box)
     w = _weights(rng, n, weights)
     return xyz, w
 
@@ -89,18 +93,20 @@ def in_sector(xyz):
             & (dec >= SECTOR_DEC[0]) & (dec <= SECTOR_DEC[1]))
 
 
-def sector_randoms(n: int, seed: int):
-    """Uniform in the sector volume: RA uniform, sin(Dec) uniform, r^3 uniform."""
+def sector_randoms(n: int, seed: int, snap: bool = True):
+    """Uniform in the sector volume: RA uniform, sin(Dec) uniform, r^3 uniform
+    (snap=False: raw float64, off the dyadic grid)."""
     rng = np.random.default_rng(seed)
     ra = rng.uniform(SECTOR_RA[0], SECTOR_RA[1], size=n)
     sdec = rng.uniform(np.sin(SECTOR_DEC[0]), np.sin(SECTOR_DEC[1]), size=n)
     r3 = rng.uniform(SECTOR_R[0] ** 3, SECTOR_R[1] ** 3, size=n)
     r = np.cbrt(r3)
     cdec = np.sqrt(1.0 - sdec * sdec)
-    return snap_dyadic(np.stack([r * cdec * np.cos(ra), r * cdec * np.sin(ra), r * sdec], axis=1))
+    xyz = np.stack([r * cdec * np.cos(ra), r * cdec * np.sin(ra), r * sdec], axis=1)
+    return snap_dyadic(xyz) if snap else xyz
 
 
-def sector_data(n: int, seed: int, sigma: float = 5.0, per_parent: float = 100.0):
+def sector_data(n: int, seed: int, sigma: float = 5.0, per_parent: float = 100.0, snap: bool = True):
     """Thomas process in the sector's bounding box (5 sigma margin), clipped to
     the sector, then exactly n points drawn without replacement."""
     rng = np.random.default_rng(seed)
@@ -122,7 +128,8 @@ def sector_data(n: int, seed: int, sigma: float = 5.0, per_parent: float = 100.0
             break
         total = int(total * 1.2)
     pick = rng.choice(xyz.shape[0], size=n, replace=False)
-    return snap_dyadic(xyz[np.sort(pick)])
+    xyz = xyz[np.sort(pick)]
+    return snap_dyadic(xyz) if snap else xyz
 
 
 # ---------------------------------------------------------------------------
@@ -204,8 +211,9 @@ def fibonacci_sphere(n: int) -> np.ndarray:
     return snap_dyadic(np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1))
 
 
-def sphere_cap(n: int, seed: int, theta_cap: float = 0.3, centre=(0.2, -0.3, 0.93)) -> np.ndarray:
-    """n random directions uniform in a spherical cap (snapped to 2^-20)."""
+def sphere_cap(n: int, seed: int, theta_cap: float = 0.3, centre=(0.2, -0.3, 0.93), snap: bool = True) -> np.ndarray:
+    """n random directions uniform in a spherical cap (snapped to 2^-20, or
+    exact unit vectors with snap=False)."""
     rng = np.random.default_rng(seed)
     c = np.asarray(centre, dtype=np.float64)
     c /= np.linalg.norm(c)
@@ -220,7 +228,7 @@ def sphere_cap(n: int, seed: int, theta_cap: float = 0.3, centre=(0.2, -0.3, 0.9
         k = v / sn
         K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
         local = local @ (np.eye(3) + sn * K + (1 - cs) * K @ K).T
-    return snap_dyadic(local)
+    return snap_dyadic(local) if snap else local / np.linalg.norm(local, axis=1, keepdims=True)
 
 
 def sphere_field(xyz: np.ndarray, seed: int, nblobs: int = 64, width: float = 0.05, noise: float = 0.1):

@@ -297,6 +297,22 @@ def test_alm_contracts_to_zeta():
         assert np.allclose(zz, z[l], rtol=1e-12, atol=1e-12 * np.abs(z).max())
 
 
+def test_contract_reproduces_zeta():
+    """oracle.contract on the oracle's own a_lm rows gives oracle.zeta, for a
+    primary subset with negative weights and in open space."""
+    xyz, w = small_cat(seed=9, n=400)
+    w = w * np.where(np.arange(w.size) % 3 == 0, -1.0, 1.0)
+    kw = dict(rmin=3.0, rmax=45.0, nbins=5, lmax=6)
+    prim = np.random.default_rng(3).choice(xyz.shape[0], 150, replace=False)
+    for box in (200.0, 0.0):
+        a = oracle.alm(xyz, w, box, prim=prim, **kw)
+        z = oracle.zeta(xyz, w, box, prim=prim, **kw)["zeta"]
+        zc = oracle.contract(a, w[prim], kw["lmax"])
+        assert np.allclose(zc, z, rtol=1e-12, atol=1e-12 * np.abs(z).max())
+    with pytest.raises(ValueError):
+        oracle.contract(a[:, :, :-1], w[prim], kw["lmax"])
+
+
 def test_argument_checks():
     xyz, w = small_cat(n=50)
     with pytest.raises(ValueError):
@@ -326,3 +342,57 @@ def test_generators_are_on_the_fixed_point_grid():
     s = synth.sector_randoms(5000, seed=6)
     assert np.all(s * 2.0 ** 20 == np.floor(s * 2.0 ** 20))
     assert np.all(synth.in_sector(s))
+
+
+# ------------------------------------------------- edge-ambiguous pairs
+
+def test_ambiguous_hand_pairs():
+    """Pairs placed at and near edges are listed with the right edge index,
+    and their count equals zeta's namb for the same tolerance."""
+    rmin, rmax, nb = 10.0, 30.0, 4          # edges 10, 15, 20, 25, 30
+    pts = np.array([[0.0, 0.0, 0.0],
+                    [15.0 + 1e-9, 0.0, 0.0],    # edge 1, just above
+                    [0.0, 25.0 - 1e-9, 0.0],    # edge 3, just below
+                    [0.0, 0.0, 30.0],           # edge 4 (r_max), on it
+                    [0.0, 0.0, -17.5]])         # mid-bin: not ambiguous
+    idx, d, r, edge = oracle.ambiguous(pts, 0.0, rmin, rmax, nb, 1e-8, prim=np.array([0]))
+    assert [tuple(x) for x in idx] == [(0, 1), (0, 2), (0, 3)]
+    assert list(edge) == [1, 3, 4]
+    np.testing.assert_allclose(r, [15.0 + 1e-9, 25.0 - 1e-9, 30.0])
+    np.testing.assert_allclose(d[2], [0.0, 0.0, 30.0])
+    full = oracle.ambiguous(pts, 0.0, rmin, rmax, nb, 1e-8)
+    z = oracle.zeta(pts, None, 0.0, rmin, rmax, nb, 0, amb_tol=1e-8)
+    assert len(full[0]) == z["namb"]
+
+
+def test_bin_flip_bound_covers_planted_flips():
+    """Secondaries planted just above edges, then moved just below them (a
+    binning of rounded coordinates could do that): the change of zeta stays
+    within the bound built from the unmoved catalogue's ambiguous pairs."""
+    from tests.parity import bin_flip_bound
+    rng = np.random.default_rng(12)
+    box = 200.0
+    kw = dict(box=box, rmin=4.0, rmax=40.0, nbins=6, lmax=6)
+    xyz, w = small_cat(seed=13, n=400, box=box)
+    prim = np.array([3, 50, 51, 200])
+    edges = kw["rmin"] + np.arange(kw["nbins"] + 1) * (kw["rmax"] - kw["rmin"]) / kw["nbins"]
+    planted, moved = [], []
+    for k, p in enumerate(prim):
+        for e in (edges[0], edges[2], edges[6], edges[(k % 5) + 1]):
+            u = rng.normal(size=3)
+            u /= np.linalg.norm(u)
+            planted.append(np.mod(xyz[p] + (e + 2e-9) * u, box))
+            moved.append(np.mod(xyz[p] + (e - 2e-9) * u, box))
+    x0 = np.vstack([xyz, planted])
+    x1 = np.vstack([xyz, moved])
+    ww = np.concatenate([w, rng.uniform(0.5, 1.5, len(planted))])
+    z0 = oracle.zeta(x0, ww, prim=prim, **kw)
+    z1 = oracle.zeta(x1, ww, prim=prim, **kw)
+    amb = oracle.ambiguous(x0, box, kw["rmin"], kw["rmax"], kw["nbins"], 1e-8 / kw["rmin"], prim=prim)
+    assert len(amb[0]) >= len(planted)
+    bz, bp, outer = bin_flip_bound(x0, ww, kw, prim, amb)
+    dz = np.abs(z1["zeta"] - z0["zeta"])
+    assert dz.max() > 1e-3 * np.abs(z0["zeta"]).max()      # the flips do change zeta
+    assert np.all(dz <= bz * (1 + 1e-9) + 1e-9 * np.abs(z0["zeta"]).max())
+    assert np.all(np.abs(z1["wpairs"] - z0["wpairs"]) <= bp * (1 + 1e-9) + 1e-12)
+    assert abs(z1["npairs"] - z0["npairs"]) <= outer
