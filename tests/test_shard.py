@@ -1,8 +1,10 @@
 """Multi-rank decomposition of zeta over primaries: world size 2, gloo, CPU.
 
-The partial zeta of each rank's primary shard comes from the FP64 oracle
-here (no GPU); the test checks that the shards partition the primaries and
-that the float64 all-reduce of the partials reproduces the full zeta.
+Each rank runs shard.sharded_zeta itself -- the product's multi-GPU step:
+its shard of the primaries, compute_subset over that shard, then the float64
+all-reduce -- with an estimator stand-in whose compute_subset is the FP64
+oracle (no GPU here).  The test checks that every rank ends with the full
+zeta and that the shards partition the primaries.
 """
 import os
 import socket
@@ -22,18 +24,31 @@ def _free_port():
         return s.getsockname()[1]
 
 
+class OracleEstimator:
+    """Stands in for ctb.CTB in sharded_zeta: the same n / compute_subset
+    interface, computed by the FP64 oracle; records the primaries it got."""
+
+    def __init__(self, xyz, w, kw):
+        self.xyz, self.w, self.kw = xyz, w, kw
+        self.n = xyz.shape[0]
+        self.seen = None
+
+    def compute_subset(self, prim):
+        import oracle
+        self.seen = np.asarray(prim)
+        return oracle.zeta(self.xyz, self.w, prim=self.seen, nthreads=1, **self.kw)["zeta"]
+
+
 def _worker(rank, world, port, out):
     import torch.distributed as dist
-    import oracle
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     xyz, w = synth.thomas(1500, 200.0, 15, 4.0, seed=31, weights="u0.5-1.5")
-    prim = shard.shard_primaries(xyz.shape[0], rank, world, seed=5)
-    part = oracle.zeta(xyz, w, prim=prim, nthreads=1, **KW)["zeta"]
-    total = shard.allreduce_zeta(part)
+    est = OracleEstimator(xyz, w, KW)
+    total = shard.sharded_zeta(est, rank, world, seed=5)
     np.save(os.path.join(out, f"z{rank}.npy"), total)
-    np.save(os.path.join(out, f"p{rank}.npy"), prim)
+    np.save(os.path.join(out, f"p{rank}.npy"), est.seen)
     dist.destroy_process_group()
 
 
@@ -57,3 +72,4 @@ def test_two_rank_allreduce_matches_full(tmp_path):
     assert np.allclose(z0, full, rtol=1e-12, atol=1e-12 * np.abs(full).max())
     p0, p1 = np.load(tmp_path / "p0.npy"), np.load(tmp_path / "p1.npy")
     assert np.intersect1d(p0, p1).size == 0 and p0.size + p1.size == xyz.shape[0]
+    assert np.array_equal(p0, shard.shard_primaries(xyz.shape[0], 0, world, seed=5))
