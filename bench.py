@@ -1,17 +1,27 @@
 """Benchmark: Legendre-multipole 3PCF on one GB300 (prints one JSON line).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp32|bf16x3|tf32] [--workload thomas_1m]
+                    [--precision mixed|fp32|bf16x3|tf32] [--workload thomas_4m]
 
 A step is one full pass of the hot path over the workload: ingest + cell sort
 (ctb_set_points from device-resident float64 inputs), pair multipoles,
-contraction and the FP64 reduction (ctb_compute).  Default workload: 1,000,000
-Thomas-process points in a periodic cube L = 1000 (10,000 parents, sigma = 5,
-weights U[0.5, 1.5], seed 1), r in [5, 200] with 20 linear bins, l_max = 10.
+contraction and the FP64 reduction (ctb_compute).  Default workload: the
+precision configuration, 4,000,000 Thomas-process points in a periodic cube
+L = 2000 (40,000 parents, sigma = 5, weights U[0.5, 1.5], seed 2), r in
+[10, 200] with 32 linear bins, l_max = 20.
+
+Default precision "mixed": the same catalogue is timed in plain FP32 (FP32
+pair kernel and contraction) and then with the BF16 hi/lo tensor-core
+contraction; the line's value is the mixed form, `plain_fp32` holds the plain
+form and `mixed_over_plain` their ratio; a short TF32 run is an extra field.
 
 value  pair-multipole updates/s = binned ordered pairs x (l_max+1)^2 / step time
 e2e    the same through the C ABI with HOST float64 inputs and a HOST zeta
        (host->device copies and the result read-back inside the timed region)
+
+Under torchrun (N > 1) each rank computes its shard of the primaries of the
+one catalogue (every point a secondary) and the ranks sum zeta with one FP64
+all-reduce: one zeta per step over all GPUs (strong scaling).
 
 --impl reference times the FP64 CPU oracle (the slow, obviously correct
 restatement of the method) on a bounded sample of primaries of the same
@@ -34,7 +44,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "pair-multipole updates/s (zeta_ell 3PCF, 1 GB300)"
+METRIC = "pair-multipole updates/s and ms per zeta_ell at 1 GB300 (mixed vs plain FP32, <=1e-3 rel err)"
 UNIT = "updates/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
@@ -43,8 +53,9 @@ SM_COUNT = 152
 INST_PER_UPDATE = 2.6
 # DRAM bytes per pair of the accumulation kernel from one ncu capture of the
 # current k_alm (dram__bytes_read.sum + dram__bytes_write.sum over the pairs of
-# the captured launch); None when the kernel changed after the capture.
-K_ALM_DRAM_BYTES_PER_PAIR = 4.395
+# the captured launch).
+# Keyed by l_max; a missing entry reports null traffic.
+K_ALM_DRAM_BYTES_PER_PAIR = {10: 4.395}
 FP32_LANES_PER_SM = 128
 
 
@@ -177,30 +188,31 @@ def flops_per_pair(lmax: int) -> int:
     return f
 
 
-def traffic_per_launch(npairs: int, chunks: int):
+def traffic_per_launch(lmax: int, npairs: int, chunks: int):
     """DRAM bytes of one mean k_alm launch of this run, scaled from the
     captured launch by its pairs (the traffic is the list words, which grow
-    with the pairs), or None."""
-    if K_ALM_DRAM_BYTES_PER_PAIR is None or chunks <= 0:
+    with the pairs), or None when no capture of the current kernel exists."""
+    per_pair = K_ALM_DRAM_BYTES_PER_PAIR.get(lmax)
+    if per_pair is None or chunks <= 0:
         return None
-    return K_ALM_DRAM_BYTES_PER_PAIR * npairs / chunks
+    return per_pair * npairs / chunks
 
 
-def contraction_roofline(args, kw, stages_ms, cfg, pk, pk_kind, npts):
+def contraction_roofline(prec, kw, stages_ms, pk, pk_kind, npts):
     """Tensor-pipe roofline of the tcgen05 contraction (mixed precisions only):
     2 * primaries * (l_max+1)^2 * nbins^2 FLOPs per step (x3 for the BF16 hi/lo
     split) over the contraction stage's event time, against the measured dense
     BF16 peak (TF32: x 1.1/2.25, the nominal TF32/BF16 ratio)."""
-    if args.precision == "fp32" or stages_ms.get("contraction", 0.0) <= 0.0:
+    if prec == "fp32" or kw.get("sphere") or stages_ms.get("contraction", 0.0) <= 0.0:
         return {}
     nc = ncoef(kw)
-    flops = 2.0 * npts * nc * kw["nbins"] ** 2 * (3 if args.precision == "bf16x3" else 1)
-    peak = float(pk.get("bf16_tflops", 1900.0)) * (1.0 if args.precision == "bf16x3" else 1.1 / 2.25)
+    flops = 2.0 * npts * nc * kw["nbins"] ** 2 * (3 if prec == "bf16x3" else 1)
+    peak = float(pk.get("bf16_tflops", 1900.0)) * (1.0 if prec == "bf16x3" else 1.1 / 2.25)
     achieved = flops / (stages_ms["contraction"] / 1e3) / 1e12
     return {"roofline_contraction": {"bound": "tensor", "kernel": "k_contract_tc", "achieved": achieved,
                                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                                      "peak_note": f"dense BF16 ({pk_kind}, burst)"
-                                                  + (" x 1.1/2.25 for TF32" if args.precision == "tf32" else "")}}
+                                                  + (" x 1.1/2.25 for TF32" if prec == "tf32" else "")}}
 
 
 def peaks():
@@ -287,6 +299,17 @@ def barrier(world):
         dist.barrier()
 
 
+def sum_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def max_over_ranks(world, v: float) -> float:
     if world == 1:
         return v
@@ -327,6 +350,22 @@ def zeta_err(z, ref) -> float:
     s = np.sqrt(g[:, :, None] * g[:, None, :])
     d = np.abs(np.asarray(z) - ref["zeta"])
     return float(np.max(np.where(s > 0, d / np.where(s > 0, s, 1.0), np.where(d > 0, np.inf, 0.0))))
+
+
+def zeta_err_elementwise(z, ref, floor=1e-3) -> float:
+    """Plain relative error over the entries with |zeta_ref| >= floor * max_l |zeta_ref|."""
+    zr = ref["zeta"]
+    big = (np.abs(zr) >= floor * np.abs(zr).max(axis=(1, 2), keepdims=True)) & (np.abs(zr) > 0)
+    d = np.abs(np.asarray(z) - zr)
+    return float(np.max(np.where(big, d / np.where(big, np.abs(zr), 1.0), 0.0)))
+
+
+def zeta_err_normwise(z, ref) -> float:
+    """max over l of max |dzeta_l| / max |zeta_ref_l|."""
+    zr = ref["zeta"]
+    d = np.abs(np.asarray(z) - zr).max(axis=(1, 2))
+    m = np.abs(zr).max(axis=(1, 2))
+    return float(np.max(np.where(m > 0, d / np.where(m > 0, m, 1.0), np.where(d > 0, np.inf, 0.0))))
 
 
 def oracle_rate(xyz, w, kw, target_s: float, seed: int = 7, full: bool = False):
@@ -393,6 +432,9 @@ def run_reference(args):
 # our arm
 
 
+PREC_OPT = {"fp32": 0, "bf16x3": 1, "tf32": 2}
+
+
 def run_ours(args):
     world, rank, local = dist_init(args)
     import torch
@@ -405,12 +447,18 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     xyz, w, kw, cfg = workload(args.workload)
     nc = ncoef(kw)
+    sphere = bool(kw.get("sphere"))
+    batch = isinstance(xyz, list)  # several catalogues, one ctb_compute_batch per step
+    # precisions timed in this run: "mixed" = plain FP32, then the BF16 hi/lo
+    # tensor-core contraction (the line's headline), then a short TF32 extra
+    if args.precision == "mixed":
+        modes = ["fp32"] if sphere else ["fp32", "bf16x3"]
+    else:
+        modes = [args.precision]
+    headline = modes[-1]
     est = make_estimator(ctb, kw)
     stream = torch.cuda.current_stream(dev)
     est.set_stream(stream)
-    if args.precision != "fp32":
-        est.set_option(ctb.OPT_PRECISION, {"bf16x3": ctb.PREC_BF16X3, "tf32": ctb.PREC_TF32}[args.precision])
-    batch = isinstance(xyz, list)  # several catalogues, one ctb_compute_batch per step
     if args.cells_per_rmax:
         est.set_option(ctb.OPT_CELLS_PER_RMAX, args.cells_per_rmax)
     elif not batch:
@@ -429,6 +477,11 @@ def run_ours(args):
         from paper_2604_08855_gb300 import synth
         d_prim = torch.from_numpy(synth.sample_primaries(xyz.shape[0], args.primaries, seed=7)).to(dev)
         cfg = {**cfg, "primaries": args.primaries, "note": "primary subset (profiling case)"}
+    elif world > 1 and not batch:
+        # several GPUs: each rank takes its shard of one catalogue's primaries
+        # (every point stays a secondary) and one FP64 all-reduce sums zeta
+        from paper_2604_08855_gb300 import shard
+        d_prim = torch.from_numpy(shard.shard_primaries(xyz.shape[0], rank, world)).to(dev)
 
     seq = batch and args.batch_mode == "sequential"
     seq_stats = {}
@@ -457,14 +510,51 @@ def run_ours(args):
             est.compute(out=d_zeta)
         else:
             est.compute_subset(d_prim, out=d_zeta)
+            if world > 1 and not args.primaries:
+                import torch.distributed as dist
+                dist.all_reduce(d_zeta, op=dist.ReduceOp.SUM)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize(dev)
+    def stats():
+        if seq:
+            return seq_stats["timings"], seq_stats["launches"], seq_stats["pairs"], seq_stats["chunks"]
+        return est.timings(), est.launch_count(), est.pair_count(), est.chunk_count()
+
+    def time_mode(prec, steps, warmup):
+        est.set_option(ctb.OPT_PRECISION, PREC_OPT[prec])
+        for _ in range(warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches, stages = 0, []
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        wall0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            tm, ln, npairs, chunks = stats()
+            launches += ln
+            stages.append(tm)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - wall0
+        barrier(world)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        t_total = max_over_ranks(world, sum(step_ms) / 1e3)
+        npairs_all = int(sum_over_ranks(world, float(npairs))) if world > 1 and d_prim is not None \
+            and not args.primaries else npairs
+        return {"t_total": t_total, "stages": np.mean(np.array(stages), axis=0), "launches": launches,
+                "npairs": npairs, "npairs_all": npairs_all, "chunks": chunks, "wall": wall,
+                "pair_ms": float(np.mean([s[7] for s in stages]))}
 
     shared_info = None
     if shared_h is not None:
+        est.set_option(ctb.OPT_PRECISION, PREC_OPT[headline])
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
         # the exact estimator on the same catalogue, once, for the speed and the deviation
         est.set_points(d_xyz, d_w)
         t0 = torch.cuda.Event(enable_timing=True)
@@ -491,38 +581,63 @@ def run_ours(args):
                        "dev_metric": dev_metric + ", against the exact path on the GPU"}
         torch.cuda.synchronize(dev)
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    pair_ms, launches, npairs, stages = [], 0, 0, []
-    barrier(world)
-    torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
-        wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-            if seq:
-                tm = seq_stats["timings"]
-                launches += seq_stats["launches"]
-                npairs, chunks = seq_stats["pairs"], seq_stats["chunks"]
-            else:
-                tm = est.timings()
-                launches += est.launch_count()
-                npairs = est.pair_count()
-                chunks = est.chunk_count()
-            pair_ms.append(tm[7])
-            stages.append(tm)
-        torch.cuda.synchronize(dev)
-        wall = time.perf_counter() - wall0
-    barrier(world)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = max_over_ranks(world, sum(step_ms) / 1e3)
-    updates = npairs * nc
-    value = world * args.steps * updates / t_total
-    ms_per_step = 1e3 * t_total / args.steps
+        res = {}
+        for prec in modes:
+            res[prec] = time_mode(prec, args.steps, args.warmup)
+        clocks = clk.summary()
+    extra_tf32 = None
+    if args.precision == "mixed" and not sphere and not batch and shared_h is None and args.tf32_steps > 0:
+        extra_tf32 = time_mode("tf32", args.tf32_steps, 1)
+    est.set_option(ctb.OPT_PRECISION, PREC_OPT[headline])
 
-    # end to end through the public API with host buffers
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    # FP32 lane-instruction peak (one FMA-pipe instruction per lane per clock)
+    peak_tinst = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    n_groups = (kw["mmax"] if sphere else kw["lmax"]) + 1
+    names = ["ingest", "sort_grid", "pair_total", "pack", "contraction", "reduce", "enumerate", "accumulate",
+             "group"]
+
+    def summarise(prec, r):
+        updates = r["npairs_all"] * nc
+        value = args.steps_of(prec) * updates / r["t_total"]
+        ms = 1e3 * r["t_total"] / args.steps_of(prec)
+        pair_s = r["pair_ms"] / 1e3
+        if sphere:
+            inst_pair = 4 * kw["mmax"] + 11
+            achieved = r["npairs"] * inst_pair / pair_s / 1e12
+            roof = {"kernel": "k_am", "work_per_unit": f"{inst_pair} FP32 instructions per pair (4 m_max + 11)"}
+        else:
+            # algorithmic work of the accumulation: INST_PER_UPDATE FP32 instructions
+            # per (pair, coefficient) update, over the kernel's own event time
+            achieved = r["npairs"] * nc * INST_PER_UPDATE / pair_s / 1e12
+            impl_tflops = r["npairs"] * flops_per_pair(kw["lmax"]) / pair_s / 1e12
+            roof = {"kernel": "k_alm", "work_per_unit": f"{INST_PER_UPDATE} FP32 instructions per update",
+                    "traffic": traffic_per_launch(kw["lmax"], r["npairs"], r["chunks"]),
+                    "impl_flops_per_pair": flops_per_pair(kw["lmax"]), "impl_tflops": impl_tflops,
+                    "impl_frac": impl_tflops / (2 * peak_tinst)}
+        stages_ms = {k: round(float(v), 3) for k, v in zip(names, r["stages"])}
+        out = {
+            "value": value, "ms_per_step": ms, "ms_per_zeta_ell": ms / n_groups,
+            "pairs_per_step": r["npairs_all"], "pairs_per_s": args.steps_of(prec) * r["npairs_all"] / r["t_total"],
+            "stages_ms": stages_ms, "gpu_launches": r["launches"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+                         "frac": achieved / peak_tinst, "traffic": None, **roof, "launches_per_step": r["chunks"],
+                         "peak_note": f"FP32 pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
+                                      f"{sm_max:.0f} MHz ({pk_kind} max clock), burst",
+                         "kernel_ms": 1e3 * pair_s},
+        }
+        n_prim_step = (sum(a.shape[0] for a in xyz) if batch else xyz.shape[0]) if not args.primaries \
+            else args.primaries
+        if world > 1 and d_prim is not None and not args.primaries:
+            n_prim_step = int(d_prim.shape[0])
+        out.update(contraction_roofline(prec, kw, stages_ms, pk, pk_kind, npts=n_prim_step))
+        return out
+
+    args.steps_of = lambda prec: args.steps
+    head = summarise(headline, res[headline])
+    # end to end through the public API with host buffers (the headline precision)
     zh = np.zeros(tuple(d_zeta.shape))
     e2e_t = []
     for k in range(0 if args.no_e2e else max(2, min(args.steps, 5)) + 1):
@@ -538,71 +653,68 @@ def run_ours(args):
             est.set_points(xyz, w)
             if shared_h is not None:
                 est.compute_shared(shared_h, out=zh)
-            else:
+            elif d_prim is None:
                 est.compute(out=zh)
+            else:
+                est.compute_subset(d_prim.cpu().numpy(), out=zh)
+                if world > 1 and not args.primaries:
+                    from paper_2604_08855_gb300 import shard
+                    zh[...] = shard.allreduce_zeta(zh)
         dt = time.perf_counter() - t0
         if k > 0:
             e2e_t.append(dt)
     e2e_s = max_over_ranks(world, float(np.mean(e2e_t)) if e2e_t else float("nan"))
     in_bytes = sum(a.nbytes for a in xyz) + sum(a.nbytes for a in w) if batch else xyz.nbytes + w.nbytes
-    e2e = {"value": world * updates / e2e_s, "unit": UNIT,
+    e2e = {"value": res[headline]["npairs_all"] * nc / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(zh.nbytes + 8)}
 
-    n_prim_step = (sum(a.shape[0] for a in xyz) if batch else xyz.shape[0]) if not args.primaries \
-        else args.primaries
-    pk, pk_kind = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    # FP32 lane-instruction peak (one FMA-pipe instruction per lane per clock)
-    peak_tinst = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
-    pair_s = float(np.mean(pair_ms)) / 1e3
-    sphere = bool(kw.get("sphere"))
-    n_groups = (kw["mmax"] if sphere else kw["lmax"]) + 1
-    if sphere:
-        # per pair: the Chebyshev recurrence (2 per m: cos and sin), one
-        # accumulate per real coefficient, ~10 for the tangent projection
-        inst_pair = 4 * kw["mmax"] + 11
-        achieved = npairs * inst_pair / pair_s / 1e12
-        roof = {"kernel": "k_am", "work_per_unit": f"{inst_pair} FP32 instructions per pair (4 m_max + 11)"}
-    else:
-        # algorithmic work of the accumulation: INST_PER_UPDATE FP32 instructions
-        # per (pair, coefficient) update, over the kernel's own event time
-        achieved = npairs * nc * INST_PER_UPDATE / pair_s / 1e12
-        impl_tflops = npairs * flops_per_pair(kw["lmax"]) / pair_s / 1e12
-        roof = {"kernel": "k_alm", "work_per_unit": f"{INST_PER_UPDATE} FP32 instructions per update",
-                "traffic": traffic_per_launch(npairs, chunks),
-                "impl_flops_per_pair": flops_per_pair(kw["lmax"]), "impl_tflops": impl_tflops,
-                "impl_frac": impl_tflops / (2 * peak_tinst)}
-    st = np.mean(np.array(stages), axis=0)
-    names = ["ingest", "sort_grid", "pair_total", "pack", "contraction", "reduce", "enumerate", "accumulate",
-             "group"]
-    stages_ms = {k: round(float(v), 3) for k, v in zip(names, st)}
-    clocks = clk.summary()
+    dtype = {"fp32": "f32", "bf16x3": "f32+bf16x3", "tf32": "f32+tf32"}[headline]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**cfg, "precision": args.precision, **({"batch_mode": args.batch_mode} if batch else {}),
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "strong" if (world > 1 and d_prim is not None and not args.primaries) else "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {**cfg, "precision": headline,
+                   "precision_note": {"fp32": "FP32 pair kernel and contraction, FP64 reduce",
+                                      "bf16x3": "FP32 pair kernel, BF16 hi/lo x3 tcgen05 contraction with FP32 "
+                                                "accumulate, FP64 reduce",
+                                      "tf32": "FP32 pair kernel, TF32 tcgen05 contraction with FP32 accumulate, "
+                                              "FP64 reduce"}[headline],
+                   **({"batch_mode": args.batch_mode} if batch else {}),
                    "cells_per_rmax": args.cells_per_rmax or 8 if batch else est.grid()[0],
                    "grid": "fixed" if args.cells_per_rmax or batch else "autotuned",
                    "l2": "flushed (256 MB write) before every step",
-                   "inputs": "device-resident float64 xyz, w"},
+                   "inputs": "device-resident float64 xyz, w",
+                   **({"parallelism": f"primaries sharded over {world} GPUs, one FP64 all-reduce of zeta"}
+                      if world > 1 and d_prim is not None and not args.primaries else {})},
         "e2e": e2e,
-        "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                     "frac": achieved / peak_tinst, "traffic": None, **roof, "launches_per_step": chunks,
-                     "peak_note": f"FP32 pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
-                                  f"{sm_max:.0f} MHz ({pk_kind} max clock)",
-                     "kernel_ms": 1e3 * pair_s},
-        "stages_ms": stages_ms,
-        **contraction_roofline(args, kw, stages_ms, cfg, pk, pk_kind, npts=n_prim_step),
-        "pairs_per_step": npairs,
-        "pairs_per_s": world * args.steps * npairs / t_total,
-        "ms_per_zeta_ell": ms_per_step / n_groups,
-        "wall_s": wall,
+        "gpu_launches": head["gpu_launches"],
+        "roofline": head["roofline"],
+        **({"roofline_contraction": head["roofline_contraction"]} if "roofline_contraction" in head else {}),
+        "stages_ms": head["stages_ms"],
+        "pairs_per_step": head["pairs_per_step"],
+        "pairs_per_s": head["pairs_per_s"],
+        "ms_per_zeta_ell": head["ms_per_zeta_ell"],
+        "wall_s": res[headline]["wall"],
         "clocks": clocks,
     }
+    if len(modes) > 1:
+        plain = summarise("fp32", res["fp32"])
+        line["plain_fp32"] = {k: plain[k] for k in ("value", "ms_per_step", "ms_per_zeta_ell", "stages_ms",
+                                                    "gpu_launches", "roofline")}
+        line["plain_fp32"]["dtype"] = "f32"
+        line["mixed_over_plain"] = head["value"] / plain["value"]
+        line["mixed_over_plain_contraction"] = (
+            (plain["stages_ms"]["contraction"] + plain["stages_ms"]["pack"])
+            / max(head["stages_ms"]["contraction"] + head["stages_ms"]["pack"], 1e-9))
+    if extra_tf32 is not None:
+        args.steps_of = lambda prec: args.tf32_steps
+        t = summarise("tf32", extra_tf32)
+        line["tf32"] = {"value": t["value"], "ms_per_step": t["ms_per_step"], "stages_ms": t["stages_ms"],
+                        "steps": args.tf32_steps, "warmup": 1, "dtype": "f32+tf32",
+                        **({"roofline_contraction": t["roofline_contraction"]} if "roofline_contraction" in t else {})}
     if shared_info is not None:
-        shared_info["speedup_vs_exact"] = shared_info["exact_ms"] / ms_per_step
+        shared_info["speedup_vs_exact"] = shared_info["exact_ms"] / head["ms_per_step"]
         line["config"]["estimator"] = "shared neighbour lists for close pivots (approximate)"
         line["shared"] = shared_info
     if rank == 0 and not args.no_cpu_baseline:
@@ -612,14 +724,24 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                                 "sample": f"{k} seeded primaries x all {sx.shape[0]} secondaries"
                                           + (" of catalogue 0" if batch else "") + f", {dt:.1f} s"}
-        # the same primaries through the library, against the oracle
+        # the same primaries through the library, against the oracle, in every precision timed
         from paper_2604_08855_gb300 import synth
         prim = synth.sample_primaries(sx.shape[0], k, seed=7)
         est.set_points(sx, sw)
-        z = est.compute_subset(prim)
-        line["parity"] = {"metric": "max |dzeta| / sqrt(G(b1,b1) G(b2,b2)), G the |w_p| Gram",
-                          "value": zeta_err(z, ref), "tolerance": 1e-5 if args.precision == "fp32" else 1e-3,
-                          "sample": f"the cpu_baseline's {k} primaries", "pairs_match": est.pair_count() == ref["npairs"]}
+        par = {"metric": "max |dzeta| / sqrt(G(b1,b1) G(b2,b2)), G the |w_p| Gram",
+               "secondary": "elementwise: max |dzeta|/|zeta| over |zeta| >= 1e-3 max_l |zeta|; "
+                            "normwise: max over l of max |dzeta_l| / max |zeta_l|",
+               "sample": f"the cpu_baseline's {k} primaries"}
+        for prec in modes + (["tf32"] if extra_tf32 is not None else []):
+            est.set_option(ctb.OPT_PRECISION, PREC_OPT[prec])
+            z = est.compute_subset(prim)
+            par[prec] = {"value": zeta_err(z, ref), "tolerance": 1e-5 if prec == "fp32" else 1e-3,
+                         "elementwise": zeta_err_elementwise(z, ref), "normwise": zeta_err_normwise(z, ref),
+                         "pairs_match": est.pair_count() == ref["npairs"]}
+        par["value"] = par[headline]["value"]
+        par["tolerance"] = par[headline]["tolerance"]
+        par["pairs_match"] = all(par[p]["pairs_match"] for p in modes)
+        line["parity"] = par
     if rank == 0:
         print(json.dumps(line), flush=True)
     est.close()
@@ -628,11 +750,14 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32"])
-    ap.add_argument("--workload", default="thomas_1m")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "bf16x3", "tf32"],
+                    help="mixed (default): time plain FP32, then the BF16 hi/lo tensor-core contraction (the "
+                         "line's value), then a short TF32 extra; or one precision alone")
+    ap.add_argument("--tf32-steps", type=int, default=2, help="timed steps of the TF32 extra (0: skip)")
+    ap.add_argument("--workload", default="thomas_4m")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--primaries", type=int, default=0,
