@@ -104,42 +104,47 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def _cheb_max_m(L: int) -> int:
-    return L if L <= 10 else 3
+PASS_CAP = 136          # accumulators per pass of the accumulation kernel
+SINGLE_PASS_LMAX = 10   # up to here one pass holds every coefficient
+FIRST_PASS_M1 = 2       # above it the first (Chebyshev) pass ends at m = 2
 
 
-def _pass_end(L: int, m0: int, budget: int, cap: int = 128) -> int:
+def _coefs(L: int, m0: int, m1: int) -> int:
+    return sum((L - m + 1) * (1 if m == 0 else 2) for m in range(m0, min(m1, L) + 1))
+
+
+def _pass_end(L: int, m0: int, cap: int) -> int:
     """End column of the pass starting at m0, as the library splits them:
-    columns are added while the pass holds at most `cap` coefficients and its
-    estimated cost stays within `budget` (one instruction per Chebyshev
-    coefficient, two per Legendre one, the T_k sequence, 40 per neighbour)."""
-    mc = _cheb_max_m(L)
-    s, cost, m = 0, 40 + (L - m0 if m0 <= mc else 0), m0
+    one pass up to l_max 10; above, a first pass [0, 2], then columns are
+    added while a pass holds at most `cap` coefficients."""
+    if L <= SINGLE_PASS_LMAX:
+        return L
+    if m0 == 0:
+        return FIRST_PASS_M1
+    s, m = 0, m0
     while m <= L:
         c = (L - m + 1) * (1 if m == 0 else 2)
-        cc = c * (1 if m <= mc else 2)
-        if (s + c > cap or cost + cc > budget) and m > m0:
+        if s + c > cap and m > m0:
             break
         s += c
-        cost += cc
         m += 1
     return m - 1
 
 
-def _passes(L: int, budget: int):
+def _passes(L: int, cap: int):
     out, m0 = [], 0
     while m0 <= L:
-        m1 = _pass_end(L, m0, budget)
+        m1 = _pass_end(L, m0, cap)
         out.append((m0, m1))
         m0 = m1 + 1
     return out
 
 
 def pass_split(L: int):
-    """The m-passes of the accumulation kernel for l_max L: the smallest cost
-    budget that keeps the pass count of filling each to 128 coefficients."""
-    target = len(_passes(L, 1 << 30))
-    lo, hi = 0, 1 << 20
+    """The m-passes of the accumulation kernel for l_max L: the smallest cap
+    that keeps the pass count of filling each to PASS_CAP coefficients."""
+    target = len(_passes(L, PASS_CAP))
+    lo, hi = 1, PASS_CAP
     while lo < hi:
         mid = (lo + hi) // 2
         if len(_passes(L, mid)) <= target:
@@ -161,30 +166,26 @@ def _cpow_flops(e: int) -> int:
 def flops_per_pair(lmax: int) -> int:
     """Algorithmic FP32 FLOPs per pair of the accumulation kernel (FMA = 2),
     counted from its formulation: per m-range pass the separation norm and
-    direction (8), the Chebyshev sequence T_k(z) (columns m <= m_c: one FMA per
-    degree), the pass's first power w (x+iy)^m0 by squaring and one complex
-    multiplication (6) per further column, one FMA per coefficient (an ADD
-    where T_0 = 1 or the power itself is added), and the monic Legendre
-    recurrence (MUL + FMA per degree) for columns m > m_c."""
+    direction (8), the pass's basis sequence (Chebyshev: one FMA per degree;
+    the first column's monic recurrence: MUL + FMA per degree), the pass's
+    first power w (x+iy)^m0 by squaring, one complex multiplication (6) per
+    further column, and one FMA per moment (an ADD for degree 0)."""
     L = lmax
-    mc = _cheb_max_m(L)
     f = 0
     for m0, m1 in pass_split(L):
         f += 8
-        if m0 <= mc and L - m0 >= 2:
-            f += 1 + 2 * (L - m0 - 1)
+        K = L - m0
+        if K >= 2:
+            f += (K - 1) * (2 if m0 == 0 else 3)
         ms = max(m0, 1)
         if m0 == 0:
-            f += 1 + 2 * L                                # column 0 (Chebyshev)
+            f += 1 + 2 * L                                # column 0
         if ms <= min(m1, L):
             f += 2 + _cpow_flops(ms)                      # w (x+iy)^ms
             for m in range(ms, min(m1, L) + 1):
                 if m > ms:
                     f += 6
-                if m <= mc:
-                    f += 2 + 4 * (L - m)
-                else:
-                    f += 2 + (4 if m + 1 <= L else 0) + 7 * max(0, L - m - 1)
+                f += 2 + 4 * (L - m)                      # (+m, -m) moments
     return f
 
 

@@ -75,7 +75,7 @@ struct ctb_ctx {
   double shared_h = 0;          // pivot cell side of the last ctb_compute_shared
   int64_t ngroups = -1;         // its groups (-1: none since ctb_set_points)
   Buf counts, offsets, scan_tmp2;
-  Buf ops[4], slot_lm, lbase_d, kp_d, partial_tc, conv_off, conv_src, conv_coef;
+  Buf ops[4], slot_lm, lbase_d, kp_d, partial_tc, conv;
   uint64_t list_cap = (uint64_t)1 << 32;  // neighbour-list entries per chunk (16 GB)
   const uint32_t* batch_keys = nullptr;    // sorted keys while a batch is loaded
   cudaEvent_t ev[16] = {};
@@ -156,8 +156,7 @@ void release_all(ctb_ctx* c) {
                 &c->bbox_part, &c->lists, &c->M, &c->wprim, &c->partial, &c->zeta, &c->prim,
                 &c->counters, &c->norm, &c->slot, &c->idx64, &c->alm, &c->thr, &c->codes, &c->code_base, &c->pairsum, &c->edge_in, &c->edge_tj, &c->counts,
                 &c->offsets, &c->scan_tmp2, &c->ops[0], &c->ops[1], &c->ops[2], &c->ops[3],
-                &c->slot_lm, &c->lbase_d, &c->kp_d, &c->partial_tc, &c->conv_off, &c->conv_src,
-                &c->conv_coef, &c->gk0, &c->gv0, &c->gk1, &c->gv1, &c->glo, &c->ghi, &c->ghead, &c->gid, &c->gscan,
+                &c->slot_lm, &c->lbase_d, &c->kp_d, &c->partial_tc, &c->conv, &c->gk0, &c->gv0, &c->gk1, &c->gv1, &c->glo, &c->ghi, &c->ghead, &c->gid, &c->gscan,
                 &c->gprim, &c->gw};
   for (Buf* b : all) release(c, *b);
   c->tables_ready = false;
@@ -181,26 +180,27 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 // normalisation per slot and the slot table of the context's layout
 int ensure_tables_sphere(ctb_ctx* c) {
-  // row = [a_0, Re a_1, Im a_1, ...], padded to 32; every slot its own coefficient
+  // row = [Re a_1, Im a_1, ..., Re a_K, Im a_K, a_0], padded to 32; every
+  // slot its own coefficient.  Coefficient index i (0: a_0, 2m-1: Re a_m,
+  // 2m: Im a_m) sits in slot i - 1, a_0 in slot 2K.
   const int nc = 2 * c->lmax + 1;
   Layout& y = c->lay;
   y = Layout{};
   y.L = c->lmax;
   y.npass = 1;
   y.row = ((nc + 31) / 32) * 32;
-  for (int i = 0; i < (kLmaxCap + 1) * (kLmaxCap + 1); ++i) y.slot[i] = i < nc ? i : -1;
-  std::vector<int> coff(y.row + 1), csrc(y.row);
-  std::vector<float> ccoef(y.row, 1.f);
-  for (int k = 0; k <= y.row; ++k) coff[k] = k;
-  for (int k = 0; k < y.row; ++k) csrc[k] = k;
+  for (int i = 0; i < (kLmaxCap + 1) * (kLmaxCap + 1); ++i) y.slot[i] = i < nc ? (i == 0 ? 2 * c->lmax : i - 1) : -1;
+  // identity flush conversion (one entry per slot; padding slots map to 0)
+  std::vector<int2> tab(y.row);
+  for (int k = 0; k < y.row; ++k) {
+    const float one = k < nc ? 1.f : 0.f;
+    tab[k].x = k;
+    std::memcpy(&tab[k].y, &one, 4);
+  }
   CK(c, ensure(c, c->slot, sizeof(y.slot)));
   CK(c, cudaMemcpyAsync(c->slot.p, y.slot, sizeof(y.slot), cudaMemcpyHostToDevice, c->st));
-  CK(c, ensure(c, c->conv_off, coff.size() * sizeof(int)));
-  CK(c, ensure(c, c->conv_src, csrc.size() * sizeof(int)));
-  CK(c, ensure(c, c->conv_coef, ccoef.size() * sizeof(float)));
-  CK(c, cudaMemcpyAsync(c->conv_off.p, coff.data(), coff.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
-  CK(c, cudaMemcpyAsync(c->conv_src.p, csrc.data(), csrc.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
-  CK(c, cudaMemcpyAsync(c->conv_coef.p, ccoef.data(), ccoef.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CK(c, ensure(c, c->conv, tab.size() * sizeof(int2)));
+  CK(c, cudaMemcpyAsync(c->conv.p, tab.data(), tab.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
   CK(c, cudaStreamSynchronize(c->st));  // host sources go out of scope
   c->tables_ready = true;
   return CTB_OK;
@@ -223,15 +223,10 @@ int ensure_tables(ctb_ctx* c) {
   std::vector<int> slot_lm(c->lay.row, -1);
   for (int l = 0; l <= c->lmax; ++l)
     for (int m = -l; m <= l; ++m) slot_lm[c->lay.slot[l * l + l + m]] = l * 64 + (m + l);
-  std::vector<int> coff, csrc;
-  std::vector<float> ccoef;
-  make_conversion(c->lay, coff, csrc, ccoef);
-  CK(c, ensure(c, c->conv_off, coff.size() * sizeof(int)));
-  CK(c, ensure(c, c->conv_src, csrc.size() * sizeof(int)));
-  CK(c, ensure(c, c->conv_coef, ccoef.size() * sizeof(float)));
-  CK(c, cudaMemcpyAsync(c->conv_off.p, coff.data(), coff.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
-  CK(c, cudaMemcpyAsync(c->conv_src.p, csrc.data(), csrc.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
-  CK(c, cudaMemcpyAsync(c->conv_coef.p, ccoef.data(), ccoef.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  std::vector<int2> tab;
+  if (!make_conversion(c->lay, tab)) return fail(c, CTB_ERR_CUDA, "internal: flush conversion table overflow");
+  CK(c, ensure(c, c->conv, tab.size() * sizeof(int2)));
+  CK(c, cudaMemcpyAsync(c->conv.p, tab.data(), tab.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
   CK(c, ensure(c, c->slot_lm, slot_lm.size() * sizeof(int)));
   CK(c, cudaMemcpyAsync(c->slot_lm.p, slot_lm.data(), slot_lm.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
   CK(c, cudaStreamSynchronize(c->st));  // host sources go out of scope
@@ -703,9 +698,7 @@ int run_pairs(ctb_ctx* c, const uint32_t* dprim, int64_t np, bool contract, cons
   aa.counts = P<uint32_t>(c->counts);
   aa.offsets = P<uint32_t>(c->offsets);
   aa.M = P<float>(c->M);
-  aa.conv_off = P<int>(c->conv_off);
-  aa.conv_src = P<int>(c->conv_src);
-  aa.conv_coef = P<float>(c->conv_coef);
+  aa.conv = P<int2>(c->conv);
   aa.work = work;
   aa.nbins = nb;
   aa.row = c->lay.row;

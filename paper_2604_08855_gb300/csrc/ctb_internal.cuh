@@ -26,7 +26,7 @@ constexpr size_t kListSlackBytes = 1024;
 constexpr int kNbinsCap = CTB_NBINS_CAP;
 constexpr int kWarp = 32;
 // coefficients accumulated per pass of the pair kernel (register budget)
-constexpr int kPassCap = 128;
+constexpr int kPassCap = 136;
 
 // ---------------------------------------------------------------------------
 // grid / estimator geometry shared by the kernels
@@ -86,10 +86,19 @@ __host__ __device__ inline int row_blocks(const Geom& g) {
 // real-harmonic coefficient layout of one pair-kernel configuration
 //
 // The pair kernel accumulates the (l, m) coefficients in passes over m ranges
-// [m0, m1] (one pass when ell_max <= 10).  Within a pass the slots run over
-// l = m0..L, and for each l over m = -min(l,m1)..-m0, (0), m0..min(l,m1).
-// Pass p occupies slots [base_p, base_p + ncp_p) of a row, ncp_p the pass's
-// coefficient count rounded up to a multiple of 32.
+// [m0, m1] (one pass when ell_max <= 10).  Each pass accumulates moments of
+// its columns in one polynomial basis q_k(z), k = 0..L - m0: the Chebyshev
+// T_k for the pass that starts at m = 0, and the monic recurrence
+// polynomials of its first column, p^{m0}_{m0+k}, for the others.  Moment k
+// of column m, sum_j w_j (x+iy)^m q_k(z_j), sits in the slot of (m + k, +-m);
+// the flush turns moments into normalised a_lm by a fixed linear map.
+//
+// Slots of a pass: first the (+m, -m) pairs, for l = max(m0,1)..L and
+// m = max(m0,1)..min(l, m1), each pair on an even slot (+m) and the odd slot
+// after it (-m), so one paired FP32 instruction updates both; then, in the
+// pass that holds m = 0, the singles (l, 0) for l = 0..L.  Pass p occupies
+// slots [base_p, base_p + ncp_p) of a row, ncp_p the pass's coefficient
+// count rounded up to a multiple of 32.
 
 __host__ __device__ constexpr int coef_count(int L, int m0, int m1) {
   int s = 0;
@@ -97,7 +106,17 @@ __host__ __device__ constexpr int coef_count(int L, int m0, int m1) {
   return s;
 }
 
+// Largest l_max whose whole coefficient set is one pass (Chebyshev basis).
+constexpr int kSinglePassLmax = 10;
+// Columns of the first pass when l_max > kSinglePassLmax: the Chebyshev
+// moments lose float32 accuracy as m grows, so this pass stops at m = 2.
+constexpr int kFirstPassM1 = 2;
+
+// end column of the pass starting at m0 when every further pass holds at
+// most `cap` coefficients
 __host__ __device__ constexpr int pass_end(int L, int m0, int cap) {
+  if (L <= kSinglePassLmax) return L;
+  if (m0 == 0) return kFirstPassM1;
   int s = 0, m = m0;
   while (m <= L) {
     int c = (L - m + 1) * (m == 0 ? 1 : 2);
@@ -108,50 +127,20 @@ __host__ __device__ constexpr int pass_end(int L, int m0, int cap) {
   return m - 1;
 }
 
-// Columns accumulated as Chebyshev moments: m <= cheb_max_m(L).  Above it
-// the monic Legendre recurrence is used (its conditioning does not degrade
-// with m; the moment conversion does).
-__host__ __device__ constexpr int cheb_max_m(int L) { return L <= 10 ? L : 3; }
-
-// The passes are balanced by an estimate of their FP32 instructions per
-// neighbour: one per Chebyshev-moment coefficient, two per Legendre-
-// recurrence coefficient, the Chebyshev sequence T_k(z) (one per degree) in
-// the pass that starts with a Chebyshev column, and kPassOverhead for the
-// neighbour's load, direction and the flush.  The number of passes stays that
-// of filling each to kPassCap accumulators.
-constexpr int kPassOverhead = 40;
-
-__host__ __device__ constexpr int col_cost(int L, int m) {
-  return (L - m + 1) * (m == 0 ? 1 : 2) * (m <= cheb_max_m(L) ? 1 : 2);
-}
-
-// end column of the pass starting at m0: columns are added while the pass
-// holds at most kPassCap coefficients and costs at most `budget`
-__host__ __device__ constexpr int pass_end_budget(int L, int m0, int budget) {
-  int s = 0, cost = kPassOverhead + (m0 <= cheb_max_m(L) ? L - m0 : 0), m = m0;
-  while (m <= L) {
-    const int c = (L - m + 1) * (m == 0 ? 1 : 2);
-    if ((s + c > kPassCap || cost + col_cost(L, m) > budget) && m > m0) break;
-    s += c;
-    cost += col_cost(L, m);
-    ++m;
-  }
-  return m - 1;
-}
-
-__host__ __device__ constexpr int passes_with_budget(int L, int budget) {
+__host__ __device__ constexpr int passes_with_cap(int L, int cap) {
   int n = 0;
-  for (int m0 = 0; m0 <= L; m0 = pass_end_budget(L, m0, budget) + 1) ++n;
+  for (int m0 = 0; m0 <= L; m0 = pass_end(L, m0, cap) + 1) ++n;
   return n;
 }
 
-// the smallest budget that keeps the pass count of the plain fill
-__host__ __device__ constexpr int pass_budget(int L) {
-  const int target = passes_with_budget(L, 1 << 30);
-  int lo = 0, hi = 1 << 20;
+// The passes after the first are balanced: the smallest cap that keeps the
+// pass count of filling each to kPassCap coefficients.
+__host__ __device__ constexpr int pass_cap_all(int L) {
+  const int target = passes_with_cap(L, kPassCap);
+  int lo = 1, hi = kPassCap;
   while (lo < hi) {
     const int mid = (lo + hi) / 2;
-    if (passes_with_budget(L, mid) <= target) hi = mid;
+    if (passes_with_cap(L, mid) <= target) hi = mid;
     else lo = mid + 1;
   }
   return lo;
@@ -161,30 +150,34 @@ __host__ __device__ constexpr int pass_budget(int L) {
 // starts at column m0 (pass_end with this cap ends the pass where the
 // balanced split does)
 __host__ __device__ constexpr int pass_cap(int L, int m0) {
-  return coef_count(L, m0, pass_end_budget(L, m0, pass_budget(L)));
+  return coef_count(L, m0, pass_end(L, m0, pass_cap_all(L)));
 }
 
 __host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
 
-__host__ __device__ constexpr int n_in_l(int l, int m0, int m1) {
-  int hi = l < m1 ? l : m1;
-  if (hi < m0) return 0;
-  int k = hi - m0 + 1;
-  return m0 == 0 ? 2 * k - 1 : 2 * k;
-}
+// Flush conversion entries per slot of the pass starting at m0: a_lm of
+// column m takes the moments of degrees l - m, l - m - 2, ... (p^m_l has
+// the parity of its degree, and so does each basis polynomial).
+__host__ __device__ constexpr int conv_entries(int L, int m0) { return (L - m0) / 2 + 1; }
 
-__host__ __device__ constexpr int l_base(int l, int m0, int m1) {
+// (+m, -m) pairs of the pass [m0, m1] with degree below l
+__host__ __device__ constexpr int pairs_below(int l, int m0, int m1) {
+  const int ms = m0 < 1 ? 1 : m0;
   int s = 0;
-  for (int q = 0; q < l; ++q) s += n_in_l(q, m0, m1);
+  for (int q = ms; q < l; ++q) {
+    const int hi = q < m1 ? q : m1;
+    if (hi >= ms) s += hi - ms + 1;
+  }
   return s;
 }
 
-// slot of (l, m) inside the pass [m0, m1] (requires m0 <= |m| <= min(l, m1))
-__host__ __device__ constexpr int local_slot(int l, int m, int m0, int m1) {
-  int hi = l < m1 ? l : m1;
-  if (m0 == 0) return l_base(l, m0, m1) + (m + hi);
-  if (m < 0) return l_base(l, m0, m1) + (m + hi);
-  return l_base(l, m0, m1) + (hi - m0 + 1) + (m - m0);
+// slot of (l, m) inside the pass [m0, m1] of kernel L (requires
+// m0 <= |m| <= min(l, m1) and l <= L)
+__host__ __device__ constexpr int local_slot(int L, int l, int m, int m0, int m1) {
+  const int ms = m0 < 1 ? 1 : m0;
+  if (m == 0) return 2 * pairs_below(L + 1, m0, m1) + l;
+  const int am = m < 0 ? -m : m;
+  return 2 * (pairs_below(l, m0, m1) + (am - ms)) + (m < 0 ? 1 : 0);
 }
 
 // pair-kernel instantiation that serves a requested ell_max
@@ -215,7 +208,8 @@ unsigned long long sq_threshold(double edge, double unit);
 void fill_beta(float* beta);   // beta_lm at [l*(kLmaxCap+1)+m]
 double norm_lm(int l, int m);  // C_lm of the real orthonormal Y_l,m
 // flush conversion table of kernel L: accumulator totals -> normalised a_lm
-void make_conversion(const Layout& lay, std::vector<int>& off, std::vector<int>& src, std::vector<float>& coef);
+// (entries padded per pass to conv_entries(L, m0_p), entry-major; see AlmArgs::conv)
+bool make_conversion(const Layout& lay, std::vector<int2>& tab);
 
 // ---------------------------------------------------------------------------
 // kernels and launchers (all asynchronous on `st`)
@@ -315,9 +309,8 @@ struct AlmArgs {
   const uint32_t* offsets;        // [prim_count][nbins]
   const uint32_t* lists;
   float* M;                       // [prim_count][nbins][row]
-  const int* conv_off;            // [row + 1] flush conversion: entries of slot s are [off[s], off[s+1])
-  const int* conv_src;            //   source slot of each entry (same pass)
-  const float* conv_coef;         //   coefficient of each entry
+  const int2* conv;               // flush conversion, per pass p (at conv_pass_offset(L, p)): entry e of local
+                                  //   slot s at [e * ncp_p + s] = (source local slot, coefficient bits)
   unsigned long long* work;
   int nbins;
   int row;

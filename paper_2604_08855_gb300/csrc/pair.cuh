@@ -9,22 +9,31 @@
 //
 // GB300 design.  The neighbour lists of a primary are grouped by bin
 // (stream.cu).  One warp owns one primary: for each of its (primary, bin)
-// lists each lane takes one neighbour per step, evaluates the (l, m)
-// coefficients of the direction by recurrences in float32 registers and
-// accumulates them (one FMA per coefficient).  Up to l_max 10 one kernel
+// lists each lane takes one neighbour per step, evaluates polynomial moments
+// of the direction by recurrences in float32 registers and accumulates them
+// (one paired FMA per (+m, -m) pair of moments).  Up to l_max 10 one kernel
 // holds all coefficients; above, the m columns are split into passes of at
-// most 128 accumulators, each its own kernel and launch (see k_alm).  At the end of the list the 32
-// lanes' accumulators are summed through a shared-memory transpose, scaled by
-// the per-(l, m) normalisation and stored as the (primary, bin) row of M.
+// most kPassCap accumulators, each its own kernel and launch (see k_alm).  At
+// the end of the list the 32 lanes' accumulators are summed through a
+// shared-memory transpose, mapped to normalised a_lm and stored as the
+// (primary, bin) row of M.
 // Each list is one run, so the cross-lane reduction happens once per
 // (primary, bin), and the first loads of the next list are issued while the
 // current one is still being accumulated.
 //
-// Recurrence (real Y_lm up to a constant per (l, m), applied at the flush):
-//   (c_m + i s_m) = w (x + i y)^m           complex power, 4 FLOPs per m
-//   p_m^m = 1,  p_{m+1}^m = z,  p_l^m = z p_{l-1}^m - beta_lm p_{l-2}^m
-// p_l^m is the associated Legendre function with the (1 - z^2)^{m/2} factor
-// absorbed in (x + i y)^m and rescaled to a monic recurrence (2 FLOPs per step).
+// Moments (real Y_lm up to a fixed linear map per (l, m), applied at the flush):
+//   (c_m + i s_m) = w (x + i y)^m        one paired FMUL + FFMA per m
+//   q_k(z)        = the pass's basis: Chebyshev T_k (T_0 = 1, T_1 = z,
+//                   T_k = 2z T_{k-1} - T_{k-2}: one FMA per degree) for the
+//                   pass that starts at m = 0, else the monic recurrence
+//                   polynomials of the pass's first column m0 (q_0 = 1,
+//                   q_1 = z, q_k = z q_{k-1} - beta q_{k-2}: two per degree)
+//   S_{m,k}      += q_k (c_m, s_m)       one paired FFMA per (k, +-m)
+// The (1 - z^2)^{m/2} factor of the associated Legendre function is absorbed
+// in (x + i y)^m.  Blackwell's paired FP32 instructions (FFMA2 / FMUL2 /
+// FADD2) update the (+m, -m) accumulator pair in one issue slot; in a stream
+// of independent accumulations they reach about 1.5x the FMA throughput of
+// scalar FFMA on this part.
 #pragma once
 
 #include "ctb_internal.cuh"
@@ -42,57 +51,43 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-
-// Column m >= 1 of the Legendre recurrence, l = LL..L (template recursion keeps
-// every accumulator index a compile-time constant, so the array stays in
-// registers).
-template <int L, int M0, int M1, int M, int LL>
-__device__ __forceinline__ void column_rec(const AlmArgs& a, float* acc, float z, float cr, float ci, float p2,
-                                           float p1) {
-  if constexpr (LL <= L) {
-    const float p = fmaf(z, p1, -(a.beta[LL * (kLmaxCap + 1) + M] * p2));
-    acc[local_slot(LL, M, M0, M1)] = fmaf(p, cr, acc[local_slot(LL, M, M0, M1)]);
-    acc[local_slot(LL, -M, M0, M1)] = fmaf(p, ci, acc[local_slot(LL, -M, M0, M1)]);
-    column_rec<L, M0, M1, M, LL + 1>(a, acc, z, cr, ci, p1, p);
-  }
+// accumulator slot S of a float2 array: the even slot is .x, the odd .y
+template <int S>
+__device__ __forceinline__ float& slot_ref(float2* acc) {
+  if constexpr ((S & 1) == 0) return acc[S >> 1].x;
+  else return acc[S >> 1].y;
 }
 
-// Chebyshev column m: moments S_{m,k} += c T_k, k = K..L-m, stored in slot (m + k, +-m).
+// Pair (k, +-M) of column M: acc += q_k (c, s) for k = K..L-M (k = 0: q_0 = 1).
 template <int L, int M0, int M1, int M, int K>
-__device__ __forceinline__ void cheb_col(float* acc, const float* T, float cr, float ci) {
+__device__ __forceinline__ void column_pairs(float2* acc, const float* Q, float2 cs) {
   if constexpr (K <= L - M) {
-    if constexpr (M == 0) {
-      acc[local_slot(K, 0, M0, M1)] = fmaf(cr, T[K], acc[local_slot(K, 0, M0, M1)]);
-    } else {
-      acc[local_slot(M + K, M, M0, M1)] = fmaf(cr, T[K], acc[local_slot(M + K, M, M0, M1)]);
-      acc[local_slot(M + K, -M, M0, M1)] = fmaf(ci, T[K], acc[local_slot(M + K, -M, M0, M1)]);
-    }
-    cheb_col<L, M0, M1, M, K + 1>(acc, T, cr, ci);
+    constexpr int i = local_slot(L, M + K, M, M0, M1) >> 1;
+    if constexpr (K == 0) acc[i] = __fadd2_rn(acc[i], cs);
+    else acc[i] = __ffma2_rn(make_float2(Q[K], Q[K]), cs, acc[i]);
+    column_pairs<L, M0, M1, M, K + 1>(acc, Q, cs);
   }
 }
 
-// Columns m = M..ME with (cr, ci) = w (x + i y)^M on entry.
+// Column 0 (first pass only): acc(k, 0) += w q_k.
+template <int L, int M0, int M1, int K>
+__device__ __forceinline__ void column_zero(float2* acc, const float* Q, float w) {
+  if constexpr (K <= L) {
+    float& a = slot_ref<local_slot(L, K, 0, M0, M1)>(acc);
+    a = K == 0 ? a + w : fmaf(w, Q[K], a);
+    column_zero<L, M0, M1, K + 1>(acc, Q, w);
+  }
+}
+
+// Columns M..ME with cs = w (x + i y)^M on entry; xy = (x, y), myx = (-y, x),
+// so cs (x + i y) = cs.x xy + cs.y myx.
 template <int L, int M0, int M1, int M, int ME>
-__device__ __forceinline__ void columns_rec(const AlmArgs& a, float* acc, const float* T, float x, float y, float z,
-                                            float cr, float ci) {
+__device__ __forceinline__ void columns(float2* acc, const float* Q, float2 xy, float2 myx, float2 cs) {
   if constexpr (M <= ME) {
-    if constexpr (M <= cheb_max_m(L)) {
-      acc[local_slot(M, M, M0, M1)] += cr;  // T_0 = 1
-      acc[local_slot(M, -M, M0, M1)] += ci;
-      cheb_col<L, M0, M1, M, 1>(acc, T, cr, ci);
-    } else {
-      acc[local_slot(M, M, M0, M1)] += cr;
-      acc[local_slot(M, -M, M0, M1)] += ci;
-      if constexpr (M + 1 <= L) {
-        acc[local_slot(M + 1, M, M0, M1)] = fmaf(z, cr, acc[local_slot(M + 1, M, M0, M1)]);
-        acc[local_slot(M + 1, -M, M0, M1)] = fmaf(z, ci, acc[local_slot(M + 1, -M, M0, M1)]);
-      }
-      column_rec<L, M0, M1, M, M + 2>(a, acc, z, cr, ci, 1.f, z);
-    }
+    column_pairs<L, M0, M1, M, 0>(acc, Q, cs);
     if constexpr (M + 1 <= ME) {
-      const float nr = fmaf(cr, x, -(ci * y));
-      const float ni = fmaf(cr, y, ci * x);
-      columns_rec<L, M0, M1, M + 1, ME>(a, acc, T, x, y, z, nr, ni);
+      const float2 nx = __ffma2_rn(make_float2(cs.x, cs.x), xy, __fmul2_rn(make_float2(cs.y, cs.y), myx));
+      columns<L, M0, M1, M + 1, ME>(acc, Q, xy, myx, nx);
     }
   }
 }
@@ -103,6 +98,15 @@ __device__ __forceinline__ void cheb_seq(float* T, float z2) {
   if constexpr (K <= KMAX) {
     T[K] = fmaf(z2, T[K - 1], -T[K - 2]);
     cheb_seq<K + 1, KMAX>(T, z2);
+  }
+}
+
+// q_k = p^{M0}_{M0+k}(z), k = K..KMAX: q_k = z q_{k-1} - beta_{M0+k, M0} q_{k-2}.
+template <int M0, int K, int KMAX>
+__device__ __forceinline__ void basis_seq(const AlmArgs& a, float* Q, float z) {
+  if constexpr (K <= KMAX) {
+    Q[K] = fmaf(z, Q[K - 1], -(a.beta[(M0 + K) * (kLmaxCap + 1) + M0] * Q[K - 2]));
+    basis_seq<M0, K + 1, KMAX>(a, Q, z);
   }
 }
 
@@ -127,80 +131,103 @@ __device__ __forceinline__ void cpow(float x, float y, float& r, float& i) {
 }
 
 // Add one neighbour (weight w, unit direction x, y, z) to the pass's
-// accumulators: one FMA per coefficient, plus the Chebyshev sequence (shared
-// by all Chebyshev columns), the Legendre recurrences of the other columns,
-// and the complex power.
+// accumulators: the pass's basis sequence, the complex powers, and one
+// paired FMA per (k, +-m) moment (one FMA per moment of column 0).
 template <int L, int M0, int M1>
-__device__ __forceinline__ void accum_pass(const AlmArgs& a, float* acc, float w, float x, float y, float z) {
-  constexpr int MC = cheb_max_m(L);
-  constexpr int KMAX = M0 <= MC ? L - M0 : 1;  // highest Chebyshev degree this pass needs
-  float T[KMAX + 1 > 2 ? KMAX + 1 : 2];
-  if constexpr (M0 <= MC) {
-    T[0] = 1.f;
-    T[1] = z;
-    cheb_seq<2, KMAX>(T, z + z);
-  }
-  if constexpr (M0 == 0) {
-    if constexpr (MC >= 0) {
-      acc[local_slot(0, 0, M0, M1)] += w;
-      cheb_col<L, M0, M1, 0, 1>(acc, T, w, 0.f);
-    }
-  }
+__device__ __forceinline__ void accum_pass(const AlmArgs& a, float2* acc, float w, float x, float y, float z) {
+  constexpr int KMAX = L - M0;  // highest basis degree this pass needs
+  float Q[KMAX + 1 > 2 ? KMAX + 1 : 2];
+  Q[0] = 1.f;
+  Q[1] = z;
+  if constexpr (M0 == 0) cheb_seq<2, KMAX>(Q, z + z);
+  else basis_seq<M0, 2, KMAX>(a, Q, z);
+  if constexpr (M0 == 0) column_zero<L, M0, M1, 0>(acc, Q, w);
   constexpr int MS = M0 < 1 ? 1 : M0;
   constexpr int ME = M1 < L ? M1 : L;
   if constexpr (MS <= ME) {
     float pr, pi;
     cpow<MS>(x, y, pr, pi);  // (x + i y)^MS by squaring
-    columns_rec<L, M0, M1, MS, ME>(a, acc, T, x, y, z, w * pr, w * pi);
+    columns<L, M0, M1, MS, ME>(acc, Q, make_float2(x, y), make_float2(-y, x), make_float2(w * pr, w * pi));
   }
 }
 
-// Cross-lane sum of the NCP accumulators through shared memory: every lane
-// writes its row (stride NCP + 4 floats, so 16-byte stores of 8 consecutive
-// lanes cover all 32 banks), then lane l sums column block
-// [l * NCP/32, (l+1) * NCP/32) over the 32 rows.  Afterwards acc[0 .. NCP/32)
-// of lane l holds the warp totals of those slots.
-template <int NCP>
-__device__ __forceinline__ void smem_transpose_reduce(float* acc, float* buf, int lane) {
-  constexpr int S = NCP + 4;
-  constexpr int V = NCP / 32;
-  float* row = buf + lane * S;
+// Cross-lane sum of the accumulators through shared memory, in chunks of
+// at most kFlushChunk slots: every lane writes its chunk (stride W + 4 floats,
+// so 16-byte stores of 8 consecutive lanes cover all 32 banks), then lane l
+// sums the chunk's column block [l * W/32, (l+1) * W/32) over the 32 rows and
+// writes the totals to tot[chunk start + that block].
+constexpr int kFlushChunk = 64;
+__host__ __device__ constexpr int flush_buf_floats(int ncp) {
+  return 32 * ((ncp < kFlushChunk ? ncp : kFlushChunk) + 4);
+}
+
+template <int NCP, int C0>
+__device__ __forceinline__ void flush_chunks(const float2* acc, float* buf, float* tot, int lane) {
+  if constexpr (C0 < NCP) {
+    constexpr int W = NCP - C0 < kFlushChunk ? NCP - C0 : kFlushChunk;
+    constexpr int S = W + 4;
+    constexpr int V = W / 32;
+    float* row = buf + lane * S;
 #pragma unroll
-  for (int i = 0; i < NCP; i += 4)
-    *reinterpret_cast<float4*>(row + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
-  __syncwarp();
-  if constexpr (V == 4) {
-    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+    for (int i = 0; i < W / 2; i += 2)
+      *reinterpret_cast<float4*>(row + 2 * i) =
+          make_float4(acc[C0 / 2 + i].x, acc[C0 / 2 + i].y, acc[C0 / 2 + i + 1].x, acc[C0 / 2 + i + 1].y);
+    __syncwarp();
+    if constexpr (V == 4) {
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
 #pragma unroll
-    for (int r = 0; r < 32; r += 2) {
-      const float4 u = *reinterpret_cast<const float4*>(buf + r * S + 4 * lane);
-      const float4 v = *reinterpret_cast<const float4*>(buf + (r + 1) * S + 4 * lane);
-      s0.x += u.x; s0.y += u.y; s0.z += u.z; s0.w += u.w;
-      s1.x += v.x; s1.y += v.y; s1.z += v.z; s1.w += v.w;
+      for (int r = 0; r < 32; r += 2) {
+        const float4 u = *reinterpret_cast<const float4*>(buf + r * S + 4 * lane);
+        const float4 v = *reinterpret_cast<const float4*>(buf + (r + 1) * S + 4 * lane);
+        s0.x += u.x; s0.y += u.y; s0.z += u.z; s0.w += u.w;
+        s1.x += v.x; s1.y += v.y; s1.z += v.z; s1.w += v.w;
+      }
+      *reinterpret_cast<float4*>(tot + C0 + 4 * lane) =
+          make_float4(s0.x + s1.x, s0.y + s1.y, s0.z + s1.z, s0.w + s1.w);
+    } else if constexpr (V == 2) {
+      float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+#pragma unroll
+      for (int r = 0; r < 32; r += 2) {
+        const float2 u = *reinterpret_cast<const float2*>(buf + r * S + 2 * lane);
+        const float2 v = *reinterpret_cast<const float2*>(buf + (r + 1) * S + 2 * lane);
+        s0.x += u.x; s0.y += u.y;
+        s1.x += v.x; s1.y += v.y;
+      }
+      *reinterpret_cast<float2*>(tot + C0 + 2 * lane) = make_float2(s0.x + s1.x, s0.y + s1.y);
+    } else {
+      float sm[V];
+#pragma unroll
+      for (int c = 0; c < V; ++c) sm[c] = 0.f;
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+#pragma unroll
+        for (int c = 0; c < V; ++c) sm[c] += buf[r * S + V * lane + c];
+#pragma unroll
+      for (int c = 0; c < V; ++c) tot[C0 + V * lane + c] = sm[c];
     }
-    acc[0] = s0.x + s1.x; acc[1] = s0.y + s1.y; acc[2] = s0.z + s1.z; acc[3] = s0.w + s1.w;
-  } else if constexpr (V == 2) {
-    float2 s0 = make_float2(0.f, 0.f), s1 = s0;
-#pragma unroll
-    for (int r = 0; r < 32; r += 2) {
-      const float2 u = *reinterpret_cast<const float2*>(buf + r * S + 2 * lane);
-      const float2 v = *reinterpret_cast<const float2*>(buf + (r + 1) * S + 2 * lane);
-      s0.x += u.x; s0.y += u.y;
-      s1.x += v.x; s1.y += v.y;
-    }
-    acc[0] = s0.x + s1.x; acc[1] = s0.y + s1.y;
-  } else {
-    float s[V];
-#pragma unroll
-    for (int c = 0; c < V; ++c) s[c] = 0.f;
-#pragma unroll
-    for (int r = 0; r < 32; ++r)
-#pragma unroll
-      for (int c = 0; c < V; ++c) s[c] += buf[r * S + V * lane + c];
-#pragma unroll
-    for (int c = 0; c < V; ++c) acc[c] = s[c];
+    __syncwarp();  // the buffer is rewritten by the next chunk
+    flush_chunks<NCP, C0 + W>(acc, buf, tot, lane);
   }
-  __syncwarp();
+}
+
+// Flush conversion of one pass, padded to E entries per slot and stored
+// entry-major in shared memory: entry e of local slot s at tab[e * NCP + s],
+// as (source local slot, coefficient bits); unused entries have coefficient
+// 0.  Lane l maps slots l, l + 32, ...: out[s] = sum_e coef * tot[src], the
+// loads of every entry independent of each other.
+template <int NCP, int E>
+__device__ __forceinline__ void flush_store(const int2* tab, const float* tot, float* __restrict__ out, int lane) {
+#pragma unroll
+  for (int i = 0; i < NCP / 32; ++i) {
+    const int s = lane + 32 * i;
+    float v = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int2 t = tab[e * NCP + s];
+      v = fmaf(__int_as_float(t.y), tot[t.x], v);
+    }
+    __stcs(out + s, v);
+  }
 }
 
 // One neighbour list run: records [off, off + n) of the lists buffer.
@@ -208,10 +235,12 @@ struct Run {
   uint32_t off, n;
 };
 
-// Loads in flight for the next iteration: two record words and one neighbour.
+// Loads in flight, for steps t, t + 1 and t + 2 of the concatenated runs:
+// the neighbours of the next two steps (q0, q1; j0, j1 their record words,
+// kNone for a lane without one) and the record word of the step after.
 struct Prefetch {
-  uint32_t j0, j1;
-  uint4 q0;
+  uint32_t j0, j1, j2;
+  uint4 q0, q1;
 };
 
 // Record of iteration t of the concatenated runs [cur | nxt] (T = iterations of cur).
@@ -225,14 +254,20 @@ __device__ __forceinline__ uint32_t rec_at(const uint32_t* __restrict__ lists, R
   return k < nxt.n ? __ldcs(lists + nxt.off + k) : kNone;
 }
 
-// Loads of the first two iterations of the concatenated runs [r | nxt].
+__device__ __forceinline__ uint4 gather(const uint4* __restrict__ pts, uint32_t j, uint4 P) {
+  return j != kNone ? __ldg(pts + j) : P;
+}
+
+// Loads of the first three iterations of the concatenated runs [r | nxt].
 __device__ __forceinline__ Prefetch prefetch_start(const uint32_t* lists, const uint4* pts, Run r, Run nxt,
                                                    uint4 P, int lane) {
   Prefetch pf;
   const uint32_t T = (r.n + 31u) / 32u;
   pf.j0 = rec_at(lists, r, nxt, T, 0, lane);
   pf.j1 = rec_at(lists, r, nxt, T, 1, lane);
-  pf.q0 = pf.j0 != kNone ? __ldg(pts + pf.j0) : P;
+  pf.j2 = rec_at(lists, r, nxt, T, 2, lane);
+  pf.q0 = gather(pts, pf.j0, P);
+  pf.q1 = gather(pts, pf.j1, P);
   return pf;
 }
 
@@ -244,8 +279,10 @@ struct Step3D {
   // Each launch runs one m-pass, so the full-lane copy of the step and the
   // general one are the only code in the instruction cache.
   static constexpr bool kFullLaneLoop = true;
+  // flush conversion entries per slot: moment degrees of the same parity
+  static constexpr int kConvE = conv_entries(L, M0);
   const AlmArgs& a;
-  __device__ __forceinline__ void operator()(float* acc, float w, float dx, float dy, float dz) const {
+  __device__ __forceinline__ void operator()(float2* acc, float w, float dx, float dy, float dz) const {
     const float ir = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     accum_pass<L, M0, M1>(a, acc, w, dx * ir, dy * ir, dz * ir);
   }
@@ -258,59 +295,73 @@ struct Step3D {
 // Step::NCP accumulators.
 template <class Step>
 __device__ __forceinline__ void run_steps(const AlmArgs& a, const Step& step, Run cur, Run nxt, const uint4 P,
-                                          Prefetch& pf, float* __restrict__ out, int base, float* sbuf, int lane,
-                                          uint32_t pe) {
+                                          Prefetch& pf, float* __restrict__ out, const int2* ctab, float* sbuf,
+                                          int lane, uint32_t pe) {
   constexpr int NCP = Step::NCP;
   const uint32_t* __restrict__ lists = a.lists;
   const uint4* __restrict__ pts = a.pts;
-  float acc[NCP];
+  float2 acc[NCP / 2];
 #pragma unroll
-  for (int i = 0; i < NCP; ++i) acc[i] = 0.f;
+  for (int i = 0; i < NCP / 2; ++i) acc[i] = make_float2(0.f, 0.f);
   const uint32_t T = (cur.n + 31u) / 32u;
-  // the second record word: the previous run could not see past this run
-  // when it is a single step long, so take it from (cur, nxt)
-  pf.j1 = rec_at(lists, cur, nxt, T, 1, lane);
+  // Steps 1 and 2 of [cur | nxt]: the previous run looked only one run
+  // ahead, so when cur is shorter than that they are taken again here.
+  {
+    const uint32_t w1 = rec_at(lists, cur, nxt, T, 1, lane);
+    if (w1 != pf.j1) {
+      pf.j1 = w1;
+      pf.q1 = gather(pts, w1, P);
+    }
+    pf.j2 = rec_at(lists, cur, nxt, T, 2, lane);
+  }
   uint32_t t = 0;
   // Steps whose lanes all hold a neighbour and whose look-ahead words are in
   // this run: no validity tests, no run switch.  (The list buffer has slack
-  // past its last entry, so the L2 prefetch needs no bound here.)
+  // past its last entry, so the L2 prefetch needs no bound here.)  Two
+  // neighbour gathers are in flight and the record word one step before
+  // its gather.
   if constexpr (Step::kFullLaneLoop) {
     const uint32_t full = cur.n >> 5;
     if (t + 3u < full) {
-      // two gathers in flight: q0 = point(t), q1 = point(t + 1), j1 = word(t + 2)
-      uint4 q1 = __ldg(pts + pf.j1);
-      pf.j1 = __ldcs(lists + cur.off + 64u + (uint32_t)lane);
       const uint32_t* __restrict__ wp = lists + cur.off + 96u + (uint32_t)lane;
       const uint32_t* pp = lists + cur.off + kListPrefetchLines * 32u;
       const bool lane0 = lane == 0;
+      uint4 q0 = pf.q0, q1 = pf.q1;
+      uint32_t j2 = pf.j2;
 #pragma unroll 1
       for (; t + 3u < full; ++t) {
         if (lane0) prefetch_l2(pp);
         pp += 32;
-        const uint4 q = pf.q0;
-        pf.q0 = q1;
-        q1 = __ldg(pts + pf.j1);
-        pf.j1 = __ldcs(wp);
+        const uint4 q = q0;
+        q0 = q1;
+        q1 = __ldg(pts + j2);
+        j2 = __ldcs(wp);
         wp += 32;
         const float dx = __int2float_rn((int)(q.x - P.x));
         const float dy = __int2float_rn((int)(q.y - P.y));
         const float dz = __int2float_rn((int)(q.z - P.z));
         step(acc, __uint_as_float(q.w), dx, dy, dz);
       }
-      // back to one gather in flight: q0 = point(t) (valid), j1 = word(t + 1)
+      // t + 1 and t + 2 are full-lane steps of this run
+      pf.q0 = q0;
+      pf.q1 = q1;
       pf.j0 = 0u;
-      pf.j1 = rec_at(lists, cur, nxt, T, t + 1, lane);
+      pf.j1 = 0u;
+      pf.j2 = j2;
     }
   }
-  // the last steps of the run: partial lanes, look-ahead into the next run
+  // the last steps of the run: partial lanes, look-ahead into the next run,
+  // the same two gathers in flight
   for (; t < T; ++t) {
     const uint32_t pa = cur.off + (t + kListPrefetchLines) * 32u;
     if (lane == 0 && pa < pe) prefetch_l2(lists + pa);
     const uint4 q = pf.q0;
     const bool valid = pf.j0 != kNone;
+    pf.q0 = pf.q1;
     pf.j0 = pf.j1;
-    pf.q0 = pf.j0 != kNone ? __ldg(pts + pf.j0) : P;
-    pf.j1 = rec_at(lists, cur, nxt, T, t + 2, lane);
+    pf.q1 = gather(pts, pf.j2, P);
+    pf.j1 = pf.j2;
+    pf.j2 = rec_at(lists, cur, nxt, T, t + 3, lane);
     float dx = __int2float_rn((int)(q.x - P.x));
     float dy = __int2float_rn((int)(q.y - P.y));
     float dz = __int2float_rn((int)(q.z - P.z));
@@ -323,37 +374,22 @@ __device__ __forceinline__ void run_steps(const AlmArgs& a, const Step& step, Ru
     }
     step(acc, w, dx, dy, dz);
   }
-  smem_transpose_reduce<NCP>(acc, sbuf, lane);
-  // lane holds the warp totals of local slots [lane * V, lane * V + V); turn
-  // them into normalised a_lm: out[s] = sum_e coef_e * total[src_e]
-  // (Chebyshev moments -> Legendre values; one entry, the normalisation, for
-  // slots accumulated by the Legendre recurrence)
-  constexpr int V = NCP / 32;
-#pragma unroll
-  for (int i = 0; i < V; ++i) sbuf[lane * V + i] = acc[i];
+  // Warp totals, in chunks of at most kFlushChunk slots through the
+  // transpose buffer, into tot[slot]; then every lane maps its slots' totals
+  // to normalised a_lm: out[s] = sum_e coef_e * tot[src_e] (moments in the
+  // pass's basis -> the Legendre values of their column).
+  float* tot = sbuf + flush_buf_floats(NCP);
+  flush_chunks<NCP, 0>(acc, sbuf, tot, lane);
   __syncwarp();
-  float* o = out + lane * V;
-#pragma unroll
-  for (int i = 0; i < V; ++i) {
-    const int sl = base + lane * V + i;
-    const int e0 = __ldg(a.conv_off + sl), e1 = __ldg(a.conv_off + sl + 1);
-    float v = 0.f;
-    for (int e = e0; e < e1; ++e) v = fmaf(__ldg(a.conv_coef + e), sbuf[__ldg(a.conv_src + e) - base], v);
-    acc[i] = v;
-  }
+  flush_store<NCP, Step::kConvE>(ctab, tot, out, lane);
   __syncwarp();
-  if constexpr (V == 4) {
-    __stcs(reinterpret_cast<float4*>(o), make_float4(acc[0], acc[1], acc[2], acc[3]));
-  } else {
-#pragma unroll
-    for (int i = 0; i < V; ++i) __stcs(o + i, acc[i]);
-  }
 }
 
 template <int L, int M0, int M1>
 __device__ __forceinline__ void run_pass(const AlmArgs& a, Run cur, Run nxt, const uint4 P, Prefetch& pf,
-                                         float* __restrict__ out, int base, float* sbuf, int lane, uint32_t pe) {
-  run_steps(a, Step3D<L, M0, M1>{a}, cur, nxt, P, pf, out, base, sbuf, lane, pe);
+                                         float* __restrict__ out, const int2* ctab, float* sbuf, int lane,
+                                         uint32_t pe) {
+  run_steps(a, Step3D<L, M0, M1>{a}, cur, nxt, P, pf, out, ctab, sbuf, lane, pe);
 }
 
 // number of m-passes of kernel L, and the columns and row offset of pass P
@@ -374,12 +410,23 @@ __host__ __device__ constexpr int pass_base(int L, int P) {
   for (int p = 0; p < P; ++p) b += pass_ncp(L, p);
   return b;
 }
+// entries of the padded conversion tables of the passes before P
+__host__ __device__ constexpr int conv_pass_offset(int L, int P) {
+  int b = 0;
+  for (int p = 0; p < P; ++p) b += pass_ncp(L, p) * conv_entries(L, pass_m0(L, p));
+  return b;
+}
+__host__ __device__ constexpr size_t alm_table_bytes(int L, int P) {
+  return (size_t)pass_ncp(L, P) * conv_entries(L, pass_m0(L, P)) * sizeof(int2);
+}
 
 // resident blocks of 4 warps the register budget of a pass is sized for
 __host__ __device__ constexpr int alm_min_blocks(int ncp) { return ncp <= 64 ? 5 : (ncp <= 96 ? 4 : 3); }
 
+// per warp: the flush's transpose buffer, the slot totals, then the
+// primary's list offsets and counts
 __host__ __device__ constexpr size_t alm_smem_per_warp(int ncp) {
-  return (size_t)32 * (ncp + 4) * sizeof(float) + 2 * kNbinsCap * sizeof(uint32_t);
+  return (size_t)(flush_buf_floats(ncp) + ncp) * sizeof(float) + 2 * kNbinsCap * sizeof(uint32_t);
 }
 
 // One warp per primary: its (primary, bin) lists are consecutive runs of the
@@ -395,12 +442,17 @@ __host__ __device__ constexpr size_t alm_smem_per_warp(int ncp) {
 template <int L, int P>
 __global__ void __launch_bounds__(128, alm_min_blocks(pass_ncp(L, P))) k_alm(AlmArgs a) {
   constexpr int M0 = pass_m0(L, P), M1 = pass_m1(L, P), NCP = pass_ncp(L, P), BASE = pass_base(L, P);
+  constexpr int NTAB = NCP * conv_entries(L, M0);
   extern __shared__ float s_alm[];
+  // [the pass's conversion table | per warp: flush buffers, list offsets, counts]
+  int2* s_tab = reinterpret_cast<int2*>(s_alm);
+  for (int k = threadIdx.x; k < NTAB; k += blockDim.x) s_tab[k] = __ldg(a.conv + conv_pass_offset(L, P) + k);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  char* wbase = reinterpret_cast<char*>(s_alm) + (size_t)warp * alm_smem_per_warp(NCP);
+  char* wbase = reinterpret_cast<char*>(s_alm) + alm_table_bytes(L, P) + (size_t)warp * alm_smem_per_warp(NCP);
   float* sbuf = reinterpret_cast<float*>(wbase);
-  uint32_t* s_off = reinterpret_cast<uint32_t*>(wbase + (size_t)32 * (NCP + 4) * sizeof(float));
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(wbase + (size_t)(flush_buf_floats(NCP) + NCP) * sizeof(float));
   uint32_t* s_n = s_off + kNbinsCap;
   const int nbins = a.nbins;
   while (true) {
@@ -436,7 +488,7 @@ __global__ void __launch_bounds__(128, alm_min_blocks(pass_ncp(L, P))) k_alm(Alm
         prefetch_l2(a.lists + cur.off + (uint32_t)lane * 32u);
       Prefetch pf = prefetch_start(a.lists, a.pts, cur, nxt, Pt, lane);
       while (true) {
-        run_pass<L, M0, M1>(a, cur, nxt, Pt, pf, a.M + (ib + b) * (uint64_t)a.row + BASE, BASE, sbuf, lane, pe);
+        run_pass<L, M0, M1>(a, cur, nxt, Pt, pf, a.M + (ib + b) * (uint64_t)a.row + BASE, s_tab, sbuf, lane, pe);
         b = nb;
         if (b >= nbins) break;
         cur = nxt;
@@ -451,7 +503,7 @@ __global__ void __launch_bounds__(128, alm_min_blocks(pass_ncp(L, P))) k_alm(Alm
 
 template <int L, int P>
 int alm_occupancy_pass(int wpb) {
-  const size_t smem = (size_t)wpb * alm_smem_per_warp(pass_ncp(L, P));
+  const size_t smem = alm_table_bytes(L, P) + (size_t)wpb * alm_smem_per_warp(pass_ncp(L, P));
   if (cudaFuncSetAttribute(k_alm<L, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int nb = 0;
@@ -466,7 +518,7 @@ cudaError_t launch_passes(const AlmArgs& a, int wpb, int nsm, cudaStream_t st) {
   if constexpr (P >= pass_count(L)) {
     return cudaSuccess;
   } else {
-    const size_t smem = (size_t)wpb * alm_smem_per_warp(pass_ncp(L, P));
+    const size_t smem = alm_table_bytes(L, P) + (size_t)wpb * alm_smem_per_warp(pass_ncp(L, P));
     cudaError_t e = cudaFuncSetAttribute(k_alm<L, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int bps = alm_occupancy_pass<L, P>(wpb);

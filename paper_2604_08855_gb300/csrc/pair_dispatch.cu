@@ -1,6 +1,7 @@
 // pair_dispatch.cu -- coefficient layout, recurrence constants, and the
 // ell_max dispatch of the pair-multipole kernel.
 #include <cmath>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -32,7 +33,7 @@ void make_layout(int L, Layout* out) {
       for (int m = -hi; m <= hi; ++m) {
         int am = m < 0 ? -m : m;
         if (am < m0) continue;
-        y.slot[l * l + l + m] = base + local_slot(l, m, m0, m1);
+        y.slot[l * l + l + m] = base + local_slot(L, l, m, m0, m1);
       }
     }
     base += ncp;
@@ -97,39 +98,73 @@ static std::vector<double> monic_in_T(int l, int m) {
   return std::vector<double>(p1.begin(), p1.begin() + n + 1);
 }
 
-// Columns m <= cheb_max_m(L) hold Chebyshev moments S_{m,k} = sum w c_m T_k(z)
-// in slot (m + k, +-m); the others hold Legendre sums in slot (l, +-m).
-void make_conversion(const Layout& lay, std::vector<int>& off, std::vector<int>& src, std::vector<float>& coef) {
+// Coefficients D of p^m_l in the basis q_k = p^{m0}_{m0+k} (k <= l - m):
+// p^m_l = sum_k D_k q_k, by back substitution on the T-basis coefficients
+// (q_k has degree k with a nonzero T_k coefficient).
+static std::vector<double> monic_in_basis(int l, int m, int m0) {
+  const int n = l - m;
+  const std::vector<double> target = monic_in_T(l, m);
+  std::vector<std::vector<double>> q(n + 1);
+  for (int k = 0; k <= n; ++k) q[k] = monic_in_T(m0 + k, m0);
+  std::vector<double> r(target), d(n + 1, 0.0);
+  for (int k = n; k >= 0; --k) {
+    d[k] = r[k] / q[k][k];
+    for (int j = 0; j <= k; ++j) r[j] -= d[k] * q[k][j];
+  }
+  return d;
+}
+
+// Each pass accumulates moments S_{m,k} = sum w c_m q_k(z) of its columns in
+// slot (m + k, +-m), q_k its basis: the Chebyshev T_k for the pass that
+// starts at m = 0, else p^{m0}_{m0+k}.  Normalised a_lm = C_lm sum_k D_k S_{m,k},
+// D the coefficients of p^m_l in that basis.
+bool make_conversion(const Layout& lay, std::vector<int2>& tab) {
   const int L = lay.L;
-  const int MC = L <= 10 ? L : 3;
   std::vector<std::vector<std::pair<int, float>>> ent(lay.row);
-  for (int l = 0; l <= L; ++l) {
-    for (int m = -l; m <= l; ++m) {
-      const int am = m < 0 ? -m : m;
-      const int s = lay.slot[l * l + l + m];
-      const double nrm = norm_lm(l, m);
-      if (am <= MC) {
-        const std::vector<double> c = monic_in_T(l, am);
-        for (int k = 0; k <= l - am; ++k) {
-          const int sl = am + k, srcm = m;
-          ent[s].push_back({lay.slot[sl * sl + sl + srcm], (float)(nrm * c[k])});
+  for (int p = 0; p < lay.npass; ++p) {
+    const int m0 = lay.m0[p];
+    for (int am = m0; am <= lay.m1[p] && am <= L; ++am) {
+      for (int l = am; l <= L; ++l) {
+        const std::vector<double> d = m0 == 0 ? monic_in_T(l, am) : monic_in_basis(l, am, m0);
+        double dmax = 0.0;
+        for (double v : d) dmax = std::fmax(dmax, std::fabs(v));
+        for (int sg = (am == 0 ? 1 : -1); sg <= 1; sg += 2) {
+          const int m = sg * am;
+          const int s = lay.slot[l * l + l + m];
+          const double nrm = norm_lm(l, m);
+          for (int k = 0; k <= l - am; ++k) {
+            if (std::fabs(d[k]) <= 1e-13 * dmax) continue;  // the other parity: exactly zero
+            const int sl = am + k;
+            ent[s].push_back({lay.slot[sl * sl + sl + m], (float)(nrm * d[k])});
+          }
         }
-      } else {
-        ent[s].push_back({s, (float)nrm});
       }
     }
   }
-  off.assign(lay.row + 1, 0);
-  src.clear();
-  coef.clear();
-  for (int s = 0; s < lay.row; ++s) {
-    off[s] = (int)src.size();
-    for (auto& e : ent[s]) {
-      src.push_back(e.first);
-      coef.push_back(e.second);
+  // padded, entry-major per pass; local slot numbers
+  tab.clear();
+  for (int p = 0; p < lay.npass; ++p) {
+    const int E = conv_entries(L, lay.m0[p]), ncp = lay.ncp[p], base = lay.base[p];
+    const size_t t0 = tab.size();
+    tab.resize(t0 + (size_t)E * ncp);
+    for (int sl = 0; sl < ncp; ++sl) {
+      const auto& v = ent[base + sl];
+      if ((int)v.size() > E) return false;
+      for (int e = 0; e < E; ++e) {
+        int2 t;
+        if (e < (int)v.size()) {
+          t.x = v[e].first - base;
+          float cf = v[e].second;
+          std::memcpy(&t.y, &cf, 4);
+        } else {
+          t.x = sl;
+          t.y = 0;  // +0.0f
+        }
+        tab[t0 + (size_t)e * ncp + sl] = t;
+      }
     }
   }
-  off[lay.row] = (int)src.size();
+  return true;
 }
 
 int alm_blocks_per_sm(int L, int wpb) {

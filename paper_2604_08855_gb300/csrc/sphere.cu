@@ -15,8 +15,9 @@
 //     a_m(p, b) += w_j (cos m phi, sin m phi),   m = 0..K,
 // with cos m phi and sin m phi from X_m = 2 cos(phi) X_{m-1} - X_{m-2}
 // (two FMAs per m; the weight rides along, as the recurrence is linear).
-// Row layout per (primary, bin): [a_0, Re a_1, Im a_1, ..., Re a_K, Im a_K],
-// padded to a multiple of 32.
+// Row layout per (primary, bin): [Re a_1, Im a_1, ..., Re a_K, Im a_K, a_0],
+// padded to a multiple of 32: each (Re, Im) pair on an even slot, so one
+// paired FP32 instruction (FFMA2 / FADD2) advances or accumulates both.
 #include "pair.cuh"
 
 namespace ctb {
@@ -25,9 +26,10 @@ template <int K>
 struct StepSphere {
   static constexpr int NCP = round32(2 * K + 1);
   static constexpr bool kFullLaneLoop = true;
+  static constexpr int kConvE = 1;  // the row holds a_m itself: one identity entry per slot
   float ex, ey;      // east unit vector (its z component is zero)
   float nx, ny, nz;  // north unit vector
-  __device__ __forceinline__ void operator()(float* acc, float w, float dx, float dy, float dz) const {
+  __device__ __forceinline__ void operator()(float2* acc, float w, float dx, float dy, float dz) const {
     const float u = fmaf(ex, dx, ey * dy);
     const float v = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
     const float r2 = fmaf(u, u, v * v);
@@ -35,23 +37,18 @@ struct StepSphere {
     const float ir = rsqrtf(flat ? 1.f : r2);
     const float c = flat ? 1.f : v * ir;
     const float s = flat ? 0.f : u * ir;
-    acc[0] += w;
+    slot_ref<2 * K>(acc) += w;
     if constexpr (K >= 1) {
-      const float c2 = c + c;
-      float pc = w, ps = 0.f;          // w (cos, sin) of (m - 2) phi
-      float qc = w * c, qs = w * s;    // and of (m - 1) phi
-      acc[1] += qc;
-      acc[2] += qs;
+      const float2 c2 = make_float2(c + c, c + c);
+      float2 p = make_float2(w, 0.f);          // w (cos, sin) of (m - 2) phi
+      float2 q = make_float2(w * c, w * s);    // and of (m - 1) phi
+      acc[0] = __fadd2_rn(acc[0], q);
 #pragma unroll
       for (int m = 2; m <= K; ++m) {
-        const float rc = fmaf(c2, qc, -pc);
-        const float rs = fmaf(c2, qs, -ps);
-        acc[2 * m - 1] += rc;
-        acc[2 * m] += rs;
-        pc = qc;
-        ps = qs;
-        qc = rc;
-        qs = rs;
+        const float2 r = __ffma2_rn(c2, q, make_float2(-p.x, -p.y));
+        acc[m - 1] = __fadd2_rn(acc[m - 1], r);
+        p = q;
+        q = r;
       }
     }
   }
@@ -86,18 +83,27 @@ __device__ __forceinline__ StepSphere<0> frame_at(float x, float y, float z) {
 
 template <int K>
 constexpr size_t am_smem_per_warp() {
-  return (size_t)32 * (StepSphere<K>::NCP + 4) * sizeof(float) + 2 * kNbinsCap * sizeof(uint32_t);
+  return alm_smem_per_warp(StepSphere<K>::NCP);
+}
+template <int K>
+constexpr size_t am_table_bytes() {
+  return (size_t)StepSphere<K>::NCP * sizeof(int2);
 }
 
 // One warp per primary, one run per non-empty (primary, bin) list, as in k_alm.
 template <int K>
 __global__ void __launch_bounds__(128) k_am(AlmArgs a) {
   extern __shared__ float s_am[];
+  // [identity conversion table | per warp: flush buffers, list offsets, counts]
+  int2* s_tab = reinterpret_cast<int2*>(s_am);
+  for (int k = threadIdx.x; k < StepSphere<K>::NCP; k += blockDim.x) s_tab[k] = __ldg(a.conv + k);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  char* wbase = reinterpret_cast<char*>(s_am) + (size_t)warp * am_smem_per_warp<K>();
+  char* wbase = reinterpret_cast<char*>(s_am) + am_table_bytes<K>() + (size_t)warp * am_smem_per_warp<K>();
   float* sbuf = reinterpret_cast<float*>(wbase);
-  uint32_t* s_off = reinterpret_cast<uint32_t*>(wbase + (size_t)32 * (StepSphere<K>::NCP + 4) * sizeof(float));
+  uint32_t* s_off =
+      reinterpret_cast<uint32_t*>(wbase + (size_t)(flush_buf_floats(StepSphere<K>::NCP) + StepSphere<K>::NCP) * sizeof(float));
   uint32_t* s_n = s_off + kNbinsCap;
   const int nbins = a.nbins;
   while (true) {
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(128) k_am(AlmArgs a) {
         prefetch_l2(a.lists + cur.off + (uint32_t)lane * 32u);
       Prefetch pf = prefetch_start(a.lists, a.pts, cur, nxt, P, lane);
       while (true) {
-        run_steps(a, step, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, 0, sbuf, lane, pe);
+        run_steps(a, step, cur, nxt, P, pf, a.M + (ib + b) * (uint64_t)a.row, s_tab, sbuf, lane, pe);
         b = nb;
         if (b >= nbins) break;
         cur = nxt;
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(128) k_am(AlmArgs a) {
 
 template <int K>
 static int am_occupancy_K(int wpb) {
-  const size_t smem = (size_t)wpb * am_smem_per_warp<K>();
+  const size_t smem = am_table_bytes<K>() + (size_t)wpb * am_smem_per_warp<K>();
   if (cudaFuncSetAttribute(k_am<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_am<K>, wpb * 32, smem) != cudaSuccess) return 0;
@@ -159,7 +165,7 @@ static int am_occupancy_K(int wpb) {
 
 template <int K>
 static cudaError_t launch_am_K(const AlmArgs& a, int wpb, int nblocks, cudaStream_t st) {
-  const size_t smem = (size_t)wpb * am_smem_per_warp<K>();
+  const size_t smem = am_table_bytes<K>() + (size_t)wpb * am_smem_per_warp<K>();
   cudaError_t e = cudaFuncSetAttribute(k_am<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_am<K><<<nblocks, wpb * 32, smem, st>>>(a);
