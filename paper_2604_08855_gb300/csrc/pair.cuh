@@ -130,24 +130,74 @@ __device__ __forceinline__ void cpow(float x, float y, float& r, float& i) {
   }
 }
 
+// Degree-major order for passes of few columns: the powers of all columns
+// first, then per degree k the next basis polynomial and the moments of
+// every column that reaches degree k.  Only three basis values are live at a
+// time (against all L - m0 + 1 in column-major order), which keeps the wide
+// passes of l_max 20 within their register budget.
+template <int L, int M0, int M1, int K, int KMAX, int MS, int ME>
+__device__ __forceinline__ void degrees(const AlmArgs& a, float2* acc, const float2* cs, float w, float z, float z2,
+                                        float q2, float q1) {
+  if constexpr (K <= KMAX) {
+    float q;
+    if constexpr (K == 0) q = 1.f;
+    else if constexpr (K == 1) q = z;
+    else if constexpr (M0 == 0) q = fmaf(z2, q1, -q2);
+    else q = fmaf(z, q1, -(a.beta[(M0 + K) * (kLmaxCap + 1) + M0] * q2));
+    if constexpr (M0 == 0) {
+      float& c0 = slot_ref<local_slot(L, K, 0, M0, M1)>(acc);
+      c0 = K == 0 ? c0 + w : fmaf(w, q, c0);
+    }
+#pragma unroll
+    for (int m = MS; m <= ME; ++m) {
+      if (K <= L - m) {
+        const int i = local_slot(L, m + K, m, M0, M1) >> 1;
+        if (K == 0) acc[i] = __fadd2_rn(acc[i], cs[m - MS]);
+        else acc[i] = __ffma2_rn(make_float2(q, q), cs[m - MS], acc[i]);
+      }
+    }
+    degrees<L, M0, M1, K + 1, KMAX, MS, ME>(a, acc, cs, w, z, z2, q1, q);
+  }
+}
+
+// columns of a pass that is accumulated degree-major
+__host__ __device__ constexpr bool degree_major(int L, int m0, int m1) {
+  return (m1 < L ? m1 : L) - (m0 < 1 ? 1 : m0) + 1 <= 5;
+}
+
 // Add one neighbour (weight w, unit direction x, y, z) to the pass's
 // accumulators: the pass's basis sequence, the complex powers, and one
 // paired FMA per (k, +-m) moment (one FMA per moment of column 0).
 template <int L, int M0, int M1>
 __device__ __forceinline__ void accum_pass(const AlmArgs& a, float2* acc, float w, float x, float y, float z) {
   constexpr int KMAX = L - M0;  // highest basis degree this pass needs
-  float Q[KMAX + 1 > 2 ? KMAX + 1 : 2];
-  Q[0] = 1.f;
-  Q[1] = z;
-  if constexpr (M0 == 0) cheb_seq<2, KMAX>(Q, z + z);
-  else basis_seq<M0, 2, KMAX>(a, Q, z);
-  if constexpr (M0 == 0) column_zero<L, M0, M1, 0>(acc, Q, w);
   constexpr int MS = M0 < 1 ? 1 : M0;
   constexpr int ME = M1 < L ? M1 : L;
-  if constexpr (MS <= ME) {
-    float pr, pi;
-    cpow<MS>(x, y, pr, pi);  // (x + i y)^MS by squaring
-    columns<L, M0, M1, MS, ME>(acc, Q, make_float2(x, y), make_float2(-y, x), make_float2(w * pr, w * pi));
+  if constexpr (degree_major(L, M0, M1)) {
+    constexpr int NC = ME >= MS ? ME - MS + 1 : 1;
+    float2 cs[NC];
+    if constexpr (MS <= ME) {
+      float pr, pi;
+      cpow<MS>(x, y, pr, pi);
+      cs[0] = make_float2(w * pr, w * pi);
+      const float2 xy = make_float2(x, y), myx = make_float2(-y, x);
+#pragma unroll
+      for (int c = 1; c < NC; ++c)
+        cs[c] = __ffma2_rn(make_float2(cs[c - 1].x, cs[c - 1].x), xy, __fmul2_rn(make_float2(cs[c - 1].y, cs[c - 1].y), myx));
+    }
+    degrees<L, M0, M1, 0, KMAX, MS, ME>(a, acc, cs, w, z, z + z, 0.f, 0.f);
+  } else {
+    float Q[KMAX + 1 > 2 ? KMAX + 1 : 2];
+    Q[0] = 1.f;
+    Q[1] = z;
+    if constexpr (M0 == 0) cheb_seq<2, KMAX>(Q, z + z);
+    else basis_seq<M0, 2, KMAX>(a, Q, z);
+    if constexpr (M0 == 0) column_zero<L, M0, M1, 0>(acc, Q, w);
+    if constexpr (MS <= ME) {
+      float pr, pi;
+      cpow<MS>(x, y, pr, pi);  // (x + i y)^MS by squaring
+      columns<L, M0, M1, MS, ME>(acc, Q, make_float2(x, y), make_float2(-y, x), make_float2(w * pr, w * pi));
+    }
   }
 }
 
@@ -421,7 +471,9 @@ __host__ __device__ constexpr size_t alm_table_bytes(int L, int P) {
 }
 
 // resident blocks of 4 warps the register budget of a pass is sized for
-__host__ __device__ constexpr int alm_min_blocks(int ncp) { return ncp <= 64 ? 5 : (ncp <= 96 ? 4 : 3); }
+// (each of the SM's four schedulers holds a quarter of the registers: 3
+// warps per scheduler allow 168 registers a thread, 4 allow 128)
+__host__ __device__ constexpr int alm_min_blocks(int ncp) { return ncp <= 32 ? 5 : (ncp <= 64 ? 4 : 3); }
 
 // per warp: the flush's transpose buffer, the slot totals, then the
 // primary's list offsets and counts
