@@ -51,6 +51,7 @@ struct ctb_ctx {
   std::string err;
   // catalogue
   int64_t n = -1;
+  bool negw = true;  // the catalogue has a negative weight (from the ingest)
   Geom g{};
   double unit = 0;
   double origin[3] = {0, 0, 0};
@@ -519,10 +520,11 @@ int load_points(ctb_ctx* c, const double* xyz, const double* w, int64_t n) {
                       c->st));
   CK(c, launch_cell_start(ks, n, g.ncells, P<uint32_t>(c->cell_start), P<uint32_t>(c->scan_tmp), c->st));
   CK(c, cudaEventRecord(c->ev[2], c->st));
-  uint32_t fl = 0;
-  CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+  uint32_t fl[4] = {0, 0, 0, 0};
+  CK(c, cudaMemcpyAsync(fl, c->flags.p, sizeof(fl), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
-  if (fl) return fail(c, CTB_ERR_NONFINITE, "non-finite coordinate or weight");
+  if (fl[0]) return fail(c, CTB_ERR_NONFINITE, "non-finite coordinate or weight");
+  c->negw = fl[3] != 0;
   for (int k = 0; k < kStages; ++k) c->t_ms[k] = 0;
   c->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
   c->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
@@ -629,22 +631,26 @@ int contract_piece(ctb_ctx* c, const PairPlan& pl, int64_t off, int64_t cnt, siz
     size_t elems = 0;
     tc_layout(tf32, cnt, nb, c->lmax, lb, kp, &elems);
     const size_t esz = tf32 ? 4 : 2;
-    // the pack kernel writes every element, the K padding of each (l, bin) included
+    // the pack kernel writes every element, the K padding of each (l, bin)
+    // included: ops[2] = H (the scaled coefficients, BF16 hi or TF32), ops[3]
+    // = 2 lo (BF16 only), ops[0] = sign(w) H when some weight is negative
+    const bool signed_a = c->negw;
     for (int k = 0; k < 4; ++k) {
-      if (tf32 && (k == 1 || k == 3)) continue;
+      if (k == 1 || (k == 3 && tf32) || (k == 0 && !signed_a)) continue;
       CK(c, ensure(c, c->ops[k], elems * esz));
     }
     CK(c, ensure(c, c->lbase_d, lb.size() * 8));
     CK(c, ensure(c, c->kp_d, kp.size() * 8));
     CK(c, cudaMemcpyAsync(c->lbase_d.p, lb.data(), lb.size() * 8, cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemcpyAsync(c->kp_d.p, kp.data(), kp.size() * 8, cudaMemcpyHostToDevice, c->st));
+    void* opa = signed_a ? c->ops[0].p : c->ops[2].p;
     CK(c, launch_pack(tf32, M, wp, cnt, nb, c->lay.row, c->lmax, P<int>(c->slot), P<unsigned long long>(c->lbase_d),
-                      P<unsigned long long>(c->kp_d), c->ops[0].p, c->ops[1].p, c->ops[2].p, c->ops[3].p,
+                      P<unsigned long long>(c->kp_d), signed_a ? c->ops[0].p : nullptr, c->ops[2].p, c->ops[3].p,
                       P<unsigned int>(c->flags) + 1, c->st));
     CK(c, cudaEventRecord(*ev_pack, c->st));
-    CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), c->ops[0].p, c->ops[1].p, c->ops[2].p,
-                             c->ops[3].p, P<double>(c->partial_tc) + seg * pl.ncon * zsz, pl.ncon,
-                             P<unsigned int>(c->flags) + 1, c->inject == CTB_INJECT_STALL, c->st));
+    CK(c, launch_contract_tc(tf32, cnt, nb, c->lmax, lb.data(), kp.data(), opa, c->ops[2].p, c->ops[3].p,
+                             P<double>(c->partial_tc) + seg * pl.ncon * zsz, pl.ncon, P<unsigned int>(c->flags) + 1,
+                             c->inject == CTB_INJECT_STALL, c->st));
     // the host vectors lb / kp back the copies above: wait before releasing them
     CK(c, cudaStreamSynchronize(c->st));
   } else {
@@ -983,9 +989,12 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   CK(c, launch_cell_start(ks, N, (uint32_t)cells_all, P<uint32_t>(c->cell_start), P<uint32_t>(c->scan_tmp), c->st));
   CK(c, cudaEventRecord(c->ev[2], c->st));
   uint32_t fl = 0;
+  uint32_t fl3 = 0;
   CK(c, cudaMemcpyAsync(&fl, c->flags.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(&fl3, P<uint32_t>(c->flags) + 3, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   if (fl) return fail(c, CTB_ERR_NONFINITE, "batch: non-finite coordinate or weight");
+  c->negw = fl3 != 0;
   const double t_ingest = elapsed(c->ev[0], c->ev[1]), t_sort = elapsed(c->ev[1], c->ev[2]);
   // pair pipeline over all primaries; densities planned from the largest catalogue
   c->batch_keys = ks;

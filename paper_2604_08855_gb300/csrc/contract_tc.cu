@@ -1,17 +1,35 @@
 // contract_tc.cu -- the zeta contraction on the fifth-generation tensor cores.
 //
 // For each l the contraction  zeta~_l(b1,b2) = sum_p w_p sum_m a_lm(p,b1) a_lm(p,b2)
-// is a tall-skinny product  D_l = A_l B_l^T  with K = (primary, m) running over
-// p * (2l+1) + (m + l):
-//   A_l[b][k] = w_p a_lm(p,b)      (rows = bins, zero-padded to M = 128)
-//   B_l[b][k] =     a_lm(p,b)      (rows = bins, zero-padded to N = npad)
-// Both operands are K-major; the pack kernel writes them from the coefficient
-// rows either as a BF16 hi/lo split (a = hi + lo; D = Ah Bh + Ah Bl + Al Bh,
-// three kind::f16 products, relative error ~2^-16) or rounded to TF32 (one
-// kind::tf32 product).  FP32 accumulation happens in TMEM; every
-// kTcFlushTiles K tiles the accumulator is drained to FP64 registers (double
-// buffered in TMEM so the MMA issue never waits for the drain), and the FP64
-// totals go to a per-CTA partial that a fixed-order FP64 reduction sums.
+// is a tall-skinny symmetric rank-k update with K = (primary, m) running
+// over p * (2l+1) + (m + l).  With C = sqrt|w_p| a it is
+//   D_l = sum_k s_k C[b1][k] C[b2][k],   s_k = sign w_p.
+// The pack kernel writes, per l, H = the BF16 rounding of C and L2 =
+// 2 (C - H) in BF16 (exact: C - H fits BF16, doubling is exact), and S = s H
+// when some weight is negative (else S is H itself).  The MMAs form
+//   Z = S H^T + S L2^T = sum s (H H^T + 2 H L^T),
+// and the FP64 finalisation symmetrises: (Z + Z^T) / 2 = sum s (H H^T + H L^T
+// + L H^T) = D up to the dropped L L^T term (relative error ~2^-16, as a
+// three-product hi/lo split).  TF32: Z = S T^T with T = tf32(C).
+// Operands are K-major in tiles of one 128-byte row per bin (64 BF16 or 32
+// TF32 elements), tile-major in HBM, so one TMA box (a 3-D box: 128 bytes x
+// npad bins x one tile) reads a contiguous block; npad = nbins padded to a
+// multiple of 16, rows past nbins zero-filled by TMA.  The tiles of a
+// pipeline stage are contiguous in shared memory, [S] H [L2], and one MMA of
+// M = 64, N = 2 npad (H and L2 side by side; TF32: N = npad) covers a
+// 16-element K step: its A view starts at the stage's first tile and runs 64
+// rows on into the next tiles (or the ring's slack), so rows past npad of D
+// are products of other rows and are ignored.  The K steps of a tile
+// alternate between two accumulators.  FP32 accumulation happens in TMEM;
+// every kTcFlushTiles K tiles the accumulators are drained to FP64 registers
+// (double buffered in TMEM so the MMA issue never waits for the drain), and
+// the FP64 totals go to a per-CTA partial that a fixed-order FP64 reduction
+// sums.
+//
+// Persistent over l: one wave of CTAs splits the concatenation of every
+// l's K tiles into equal contiguous ranges, so each CTA allocates TMEM and
+// sets up its pipeline once per launch and crosses l boundaries in its range
+// (each boundary ends an accumulator flush and the partial row of that l).
 //
 // Roles per CTA (192 threads): warps 0-3 drain TMEM (warp w reads TMEM lanes
 // 32w..32w+31 = rows of D), warp 4 issues the TMA loads, warp 5 issues the
@@ -32,11 +50,11 @@
 namespace ctb {
 
 constexpr int kTcThreads = 192;
-constexpr int kTcFlushTiles = 16;
+constexpr int kTcFlushTiles = 64;
 constexpr long long kTcTimeoutCycles = 4000000000ll;  // about 2 s
 
 struct TcMaps {
-  CUtensorMap m[kLmaxCap + 1][4];  // per l: A_hi, A_lo, B_hi, B_lo  (TF32: A, -, B, -)
+  CUtensorMap m[kLmaxCap + 1][3];  // per l: A (S, or H), B = H, B_lo = L2  (TF32: S or T, T, -)
 };
 
 struct TcArgs {
@@ -46,11 +64,18 @@ struct TcArgs {
   int nsplit;
   int stages;
   int ncols;                          // TMEM columns allocated
-  unsigned int ktiles[kLmaxCap + 1];  // 128-byte K tiles per l
+  int ncol_d;                         // columns of one accumulator (the MMA's N)
+  unsigned int cum[kLmaxCap + 2];     // 128-byte K tiles of the l before l (cum[nl] = all)
   double* partial;                    // [nl][nsplit][nbins][nbins]
   unsigned int* err;                  // bit 0: a bounded wait timed out
   long long timeout_cycles;           // limit of every mbarrier wait
   int inject_stall;                   // test hook: the MMA thread first waits on a barrier nothing signals
+  int signed_a;                       // 1: the A operand is its own tensor S (some weight is negative)
+};
+
+struct TcArgsMaps {
+  TcMaps maps;
+  TcArgs args;
 };
 
 // ---------------------------------------------------------------------------
@@ -98,11 +123,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
           smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -159,36 +184,39 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor: D f32, A/B K-major, M = 128, N = npad.
+// Instruction descriptor: D f32, A/B K-major, M = 64, N = n.
 //   bits 4-5 D format (1 = f32); 7-9 A format, 10-12 B format (kind::f16: 1 = bf16;
 //   kind::tf32: 2 = tf32); 15/16 A/B major (0 = K); 17-22 N >> 3; 24-28 M >> 4.
+constexpr int kTcM = 64;
 __host__ __device__ constexpr uint32_t make_idesc(bool tf32, int n) {
   return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(128 >> 4) << 24);
+         ((uint32_t)(kTcM >> 4) << 24);
 }
 
 // ---------------------------------------------------------------------------
-// contraction kernel: grid (nsplit, nl), one K range of one l per CTA
+// contraction kernel: gridDim.x CTAs, each a contiguous range of the
+// concatenated (l, K tile) sequence; partial row blockIdx.x of each l
 
 template <bool TF32>
-__global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_constant__ TcMaps maps, TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_constant__ TcArgsMaps am) {
+  const TcMaps& maps = am.maps;
+  const TcArgs& a = am.args;
   extern __shared__ uint8_t s_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_raw) + 1023) & ~(uintptr_t)1023);
-  const int l = blockIdx.y;
   const int split = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t total = a.ktiles[l];
-  const uint32_t per = (total + a.nsplit - 1) / a.nsplit;
+  const uint32_t total = a.cum[a.nl];
+  const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
   const uint32_t t0 = (uint32_t)split * per;
   const uint32_t t1 = min(total, t0 + per);
   if (t0 >= t1) return;  // uniform for the whole CTA
-  const uint32_t ntiles = t1 - t0;
   const int S = a.stages;
-  constexpr int NA = TF32 ? 1 : 2;
-  const uint32_t A_BYTES = 128u * 128u;
-  const uint32_t B_BYTES = (uint32_t)a.npad * 128u;
-  const uint32_t STAGE = NA * (A_BYTES + B_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)S * STAGE);
+  constexpr int NB = TF32 ? 1 : 2;  // B operands: H (and L2)
+  const uint32_t T_BYTES = (uint32_t)a.npad * 128u;  // one operand tile
+  const uint32_t A_BYTES = a.signed_a ? T_BYTES : 0u;  // S, else A is the H tile
+  const uint32_t STAGE = A_BYTES + NB * T_BYTES;
+  // after the stages: the A view's overrun (64 rows), then the barriers
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)S * STAGE + (size_t)kTcM * 128u);
   uint64_t* empty = full + S;
   uint64_t* accfull = empty + S;
   uint64_t* accempty = accfull + 2;
@@ -222,66 +250,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *s_taddr;
-  const uint32_t nflush = (ntiles + kTcFlushTiles - 1) / kTcFlushTiles;
+  // the l segments of [t0, t1): [max(t0, cum[l]), min(t1, cum[l+1]))
+  int lfirst = 0;
+  while (a.cum[lfirst + 1] <= t0) ++lfirst;
 
   if (warp == 4) {
     // ---- TMA producer
     if (lane == 0) {
-      uint32_t issued = 0;
-      for (uint32_t it = 0; it < ntiles; ++it) {
-        const int s = (int)(it % S);
-        const uint32_t ph = (it / S) & 1u;
-        if (!mbar_wait(empty + s, ph ^ 1u, s_abort, a.err, a.timeout_cycles)) break;
-        uint8_t* st = sm + (size_t)s * STAGE;
-        mbar_expect_tx(full + s, STAGE);
-        const int x = (int)((t0 + it) * (TF32 ? 32u : 64u));
-        tma_load_2d(st, &maps.m[l][0], x, 0, full + s);
-        if (!TF32) tma_load_2d(st + A_BYTES, &maps.m[l][1], x, 0, full + s);
-        tma_load_2d(st + NA * A_BYTES, &maps.m[l][2], x, 0, full + s);
-        if (!TF32) tma_load_2d(st + NA * A_BYTES + B_BYTES, &maps.m[l][3], x, 0, full + s);
-        ++issued;
+      uint32_t issued = 0, it = 0;
+      bool ok = true;
+      for (int l = lfirst; ok && l < a.nl && a.cum[l] < t1; ++l) {
+        const uint32_t sb = max(t0, a.cum[l]), se = min(t1, a.cum[l + 1]);
+        for (uint32_t t = sb; t < se; ++t, ++it) {
+          const int s = (int)(it % S);
+          const uint32_t ph = (it / S) & 1u;
+          if (!mbar_wait(empty + s, ph ^ 1u, s_abort, a.err, a.timeout_cycles)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = sm + (size_t)s * STAGE;
+          mbar_expect_tx(full + s, STAGE);
+          const int z = (int)(t - a.cum[l]);  // K tile: one contiguous block of nbins rows
+          if (a.signed_a) tma_load_3d(st, &maps.m[l][0], 0, 0, z, full + s);
+          tma_load_3d(st + A_BYTES, &maps.m[l][1], 0, 0, z, full + s);
+          if (!TF32) tma_load_3d(st + A_BYTES + T_BYTES, &maps.m[l][2], 0, 0, z, full + s);
+          ++issued;
+        }
       }
       // bounded wait for this CTA's copies still in flight (the consumer may
       // give up later than this loop ends); on the normal path these phases
       // have completed and each test passes at once
       const uint32_t first = issued > (uint32_t)S ? issued - S : 0;
-      for (uint32_t it = first; it < issued; ++it) {
+      for (uint32_t k = first; k < issued; ++k) {
         const long long tw = clock64();
-        while (!mbar_try_wait(full + (it % S), (it / S) & 1u) && clock64() - tw < a.timeout_cycles) {
+        while (!mbar_try_wait(full + (k % S), (k / S) & 1u) && clock64() - tw < a.timeout_cycles) {
         }
       }
     }
   } else if (warp == 5) {
     // ---- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(TF32, a.npad);
+      // N = the B view: H and L2 side by side (BF16), or T (TF32)
+      const uint32_t idesc = make_idesc(TF32, a.ncol_d);
       // fault injection: a wait that runs out, then the ordinary abort path
-      const bool go = !a.inject_stall || mbar_wait(never, 0, s_abort, a.err, a.timeout_cycles);
-      for (uint32_t it = 0; go && it < ntiles; ++it) {
-        const int s = (int)(it % S);
-        const uint32_t ph = (it / S) & 1u;
-        const uint32_t f = it / kTcFlushTiles;
-        const uint32_t buf = f & 1u;
-        const bool first_of_flush = (it % kTcFlushTiles) == 0;
-        if (first_of_flush && f >= 2 && !mbar_wait(accempty + buf, ((f >> 1) - 1) & 1u, s_abort, a.err, a.timeout_cycles)) break;
-        if (!mbar_wait(full + s, ph, s_abort, a.err, a.timeout_cycles)) break;
-        tc_fence_after();
-        const uint32_t sa = smem_u32(sm + (size_t)s * STAGE);
-        const uint32_t a_hi = sa, a_lo = sa + A_BYTES;
-        const uint32_t b_hi = sa + NA * A_BYTES, b_lo = b_hi + B_BYTES;
-        const uint32_t d = taddr + buf * (uint32_t)a.npad;
+      bool go = !a.inject_stall || mbar_wait(never, 0, s_abort, a.err, a.timeout_cycles);
+      uint32_t it = 0, f = 0;  // f: accumulator flushes so far (buffer f & 1)
+      for (int l = lfirst; go && l < a.nl && a.cum[l] < t1; ++l) {
+        const uint32_t sb = max(t0, a.cum[l]), se = min(t1, a.cum[l + 1]);
+        for (uint32_t t = sb; go && t < se; ++t, ++it) {
+          const int s = (int)(it % S);
+          const uint32_t ph = (it / S) & 1u;
+          const uint32_t buf = f & 1u;
+          const bool first_of_flush = ((t - sb) % kTcFlushTiles) == 0;
+          const bool last_of_flush = ((t - sb) % kTcFlushTiles) == kTcFlushTiles - 1 || t + 1 == se;
+          if (first_of_flush && f >= 2 &&
+              !mbar_wait(accempty + buf, ((f >> 1) - 1) & 1u, s_abort, a.err, a.timeout_cycles)) {
+            go = false;
+            break;
+          }
+          if (!mbar_wait(full + s, ph, s_abort, a.err, a.timeout_cycles)) {
+            go = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(sm + (size_t)s * STAGE);
+          const uint32_t b_hi = sa + A_BYTES;
+          // two accumulator chains (the even and odd 16-element K steps)
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t acc0 = (first_of_flush && kk == 0) ? 0u : 1u;
-          const uint32_t ko = (uint32_t)kk * 32u;  // 32 bytes of K per MMA
-          tc_mma<TF32>(d, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), idesc, acc0);
-          if (!TF32) {
-            tc_mma<TF32>(d, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), idesc, 1u);
-            tc_mma<TF32>(d, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), idesc, 1u);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t acc0 = (first_of_flush && kk < 2) ? 0u : 1u;
+            const uint32_t ko = (uint32_t)kk * 32u;  // 32 bytes of K per MMA
+            const uint32_t d = taddr + (buf * 2u + (uint32_t)(kk & 1)) * (uint32_t)a.ncol_d;
+            tc_mma<TF32>(d, sw128_desc(sa + ko), sw128_desc(b_hi + ko), idesc, acc0);
+          }
+          tc_commit(empty + s);
+          if (last_of_flush) {
+            tc_commit(accfull + buf);
+            ++f;
           }
         }
-        tc_commit(empty + s);
-        if ((it % kTcFlushTiles) == kTcFlushTiles - 1 || it + 1 == ntiles) tc_commit(accfull + buf);
       }
       // all MMAs issued by this thread complete before TMEM is released
       tc_commit(done);
@@ -290,33 +337,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
       }
     }
   } else {
-    // ---- drain TMEM to FP64 (warps 0-3; warp w owns rows 32w..32w+31)
-    double acc[64];
-#pragma unroll
-    for (int c = 0; c < 64; ++c) acc[c] = 0.0;
+    // ---- drain TMEM to FP64 (warps 0-3).  With M = 64 row i of D lives in
+    // TMEM lane 32 (i / 16) + i % 16: warp w reads lanes 32w.. and its lanes
+    // 0-15 hold rows 16w..16w+15.  One FP64 row sum per l segment, added to
+    // partial row `split` of that l.
     const uint32_t row_addr = taddr + ((uint32_t)(warp * 32) << 16);
-    for (uint32_t f = 0; f < nflush; ++f) {
-      const uint32_t buf = f & 1u;
-      if (!mbar_wait(accfull + buf, (f >> 1) & 1u, s_abort, a.err, a.timeout_cycles)) break;
-      tc_fence_after();
+    const int r = lane < 16 ? warp * 16 + lane : 1 << 20;
+    uint32_t f = 0;
+    bool ok = true;
+    for (int l = lfirst; ok && l < a.nl && a.cum[l] < t1; ++l) {
+      const uint32_t sb = max(t0, a.cum[l]), se = min(t1, a.cum[l + 1]);
+      const uint32_t nflush = (se - sb + kTcFlushTiles - 1) / kTcFlushTiles;
+      double acc[64];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (c * 8 < a.npad) {
-          float v[8];
-          tmem_ld8(row_addr + buf * (uint32_t)a.npad + (uint32_t)(c * 8), v);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) acc[c * 8 + q] += (double)v[q];
+      for (int c = 0; c < 64; ++c) acc[c] = 0.0;
+      for (uint32_t k = 0; k < nflush; ++k, ++f) {
+        const uint32_t buf = f & 1u;
+        if (!mbar_wait(accfull + buf, (f >> 1) & 1u, s_abort, a.err, a.timeout_cycles)) {
+          ok = false;
+          break;
         }
-      }
-      tc_fence_before();
-      mbar_arrive(accempty + buf);
-    }
-    const int r = warp * 32 + lane;
-    if (r < a.nbins && !*s_abort) {
-      double* out = a.partial + (((size_t)l * a.nsplit + split) * a.nbins + r) * a.nbins;
+        tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < 64; ++c)
-        if (c < a.nbins) out[c] += acc[c];
+        for (int c = 0; c < 8; ++c) {
+          if (c * 8 < a.npad) {
+            // Z[r][col] = the two chains' S H^T plus their S L2^T (BF16)
+            const uint32_t col = buf * 2u * (uint32_t)a.ncol_d + (uint32_t)(c * 8);
+            float v[8], u[8];
+            tmem_ld8(row_addr + col, v);
+            tmem_ld8(row_addr + col + (uint32_t)a.ncol_d, u);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] += u[q];
+            if (!TF32) {
+              tmem_ld8(row_addr + col + (uint32_t)a.npad, u);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) v[q] += u[q];
+              tmem_ld8(row_addr + col + (uint32_t)a.ncol_d + (uint32_t)a.npad, u);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) v[q] += u[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[c * 8 + q] += (double)v[q];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(accempty + buf);
+      }
+      if (ok && r < a.nbins && !*s_abort) {
+        double* out = a.partial + (((size_t)l * a.nsplit + split) * a.nbins + r) * a.nbins;
+#pragma unroll
+        for (int c = 0; c < 64; ++c)
+          if (c < a.nbins) out[c] += acc[c];
+      }
     }
   }
   tc_fence_before();
@@ -338,9 +410,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
 // kPackPrims * (2l+1) elements starting at a multiple of 16 elements; span l
 // starts at 16 l^2 of the bin's concatenated spans.  Each thread converts
 // chunks of 8 consecutive elements (chunk k lies in span l = floor(sqrt(k/2)))
-// and writes them with 16-byte stores.  A = w_p a and B = a, each as a BF16
-// hi + lo pair (or rounded to TF32).  A partial last block converts element
-// by element; block 0 also writes the zeros of the K padding.
+// and writes them with 16-byte stores: C = sqrt|w_p| a as H (BF16) and
+// L2 = 2 (C - H) (BF16), or as TF32; and S = sign(w_p) H when outS is set.
+// A partial last block converts element by element; block 0 also writes the
+// zeros of the K padding.
 constexpr int kPackPrims = 16;
 constexpr int kPackThreads = 256;
 
@@ -356,59 +429,69 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+__device__ __forceinline__ float flip(float v, bool neg) { return neg ? -v : v; }
+
+// Operand layout of one l: K tiles of KT elements (one 128-byte row each),
+// tile-major: element k of bin b at ((k / KT) nbins + b) KT + k % KT, so a
+// K tile of every bin is one contiguous block that one TMA box reads.
 template <bool TF32>
-__device__ __forceinline__ void pack_store(void* outA_hi, void* outA_lo, void* outB_hi, void* outB_lo,
-                                           unsigned long long idx, const float* av, const float* v) {
+__device__ __forceinline__ unsigned long long op_index(unsigned long long lbase, int nbins, int b, unsigned long long k) {
+  constexpr unsigned long long KT = TF32 ? 32 : 64;
+  return lbase + ((k / KT) * (unsigned long long)nbins + (unsigned long long)b) * KT + k % KT;
+}
+
+// 8 consecutive elements c[i] (already scaled by sqrt|w|) with signs neg[i]
+template <bool TF32>
+__device__ __forceinline__ void pack_store(void* outS, void* outH, void* outL, unsigned long long idx, const float* c,
+                                           const bool* neg) {
   if constexpr (TF32) {
-    uint32_t ta[8], tb[8];
+    uint32_t t[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta[i]) : "f"(av[i]));
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb[i]) : "f"(v[i]));
+    for (int i = 0; i < 8; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[i]) : "f"(c[i]));
+    uint4* H = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(outH) + idx);
+    H[0] = make_uint4(t[0], t[1], t[2], t[3]);
+    H[1] = make_uint4(t[4], t[5], t[6], t[7]);
+    if (outS) {
+      uint32_t u[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) u[i] = t[i] ^ (neg[i] ? 0x80000000u : 0u);
+      uint4* Sp = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(outS) + idx);
+      Sp[0] = make_uint4(u[0], u[1], u[2], u[3]);
+      Sp[1] = make_uint4(u[4], u[5], u[6], u[7]);
     }
-    uint4* A = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(outA_hi) + idx);
-    uint4* B = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(outB_hi) + idx);
-    A[0] = make_uint4(ta[0], ta[1], ta[2], ta[3]);
-    A[1] = make_uint4(ta[4], ta[5], ta[6], ta[7]);
-    B[0] = make_uint4(tb[0], tb[1], tb[2], tb[3]);
-    B[1] = make_uint4(tb[4], tb[5], tb[6], tb[7]);
   } else {
-    float ah[8], al[8], bh[8], bl[8];
+    float h[8], l2[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      ah[i] = __bfloat162float(__float2bfloat16_rn(av[i]));
-      al[i] = av[i] - ah[i];
-      bh[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
-      bl[i] = v[i] - bh[i];
+      h[i] = __bfloat162float(__float2bfloat16_rn(c[i]));
+      l2[i] = 2.f * (c[i] - h[i]);
     }
     const unsigned long long o = idx / 8;  // 8 BF16 = 16 bytes
-    reinterpret_cast<uint4*>(outA_hi)[o] = make_uint4(pack_bf16x2(ah[0], ah[1]), pack_bf16x2(ah[2], ah[3]),
-                                                      pack_bf16x2(ah[4], ah[5]), pack_bf16x2(ah[6], ah[7]));
-    reinterpret_cast<uint4*>(outA_lo)[o] = make_uint4(pack_bf16x2(al[0], al[1]), pack_bf16x2(al[2], al[3]),
-                                                      pack_bf16x2(al[4], al[5]), pack_bf16x2(al[6], al[7]));
-    reinterpret_cast<uint4*>(outB_hi)[o] = make_uint4(pack_bf16x2(bh[0], bh[1]), pack_bf16x2(bh[2], bh[3]),
-                                                      pack_bf16x2(bh[4], bh[5]), pack_bf16x2(bh[6], bh[7]));
-    reinterpret_cast<uint4*>(outB_lo)[o] = make_uint4(pack_bf16x2(bl[0], bl[1]), pack_bf16x2(bl[2], bl[3]),
-                                                      pack_bf16x2(bl[4], bl[5]), pack_bf16x2(bl[6], bl[7]));
+    reinterpret_cast<uint4*>(outH)[o] = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
+                                                   pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
+    reinterpret_cast<uint4*>(outL)[o] = make_uint4(pack_bf16x2(l2[0], l2[1]), pack_bf16x2(l2[2], l2[3]),
+                                                   pack_bf16x2(l2[4], l2[5]), pack_bf16x2(l2[6], l2[7]));
+    if (outS)
+      reinterpret_cast<uint4*>(outS)[o] = make_uint4(
+          pack_bf16x2(flip(h[0], neg[0]), flip(h[1], neg[1])), pack_bf16x2(flip(h[2], neg[2]), flip(h[3], neg[3])),
+          pack_bf16x2(flip(h[4], neg[4]), flip(h[5], neg[5])), pack_bf16x2(flip(h[6], neg[6]), flip(h[7], neg[7])));
   }
 }
 
 template <bool TF32>
-__device__ __forceinline__ void pack_store1(void* outA_hi, void* outA_lo, void* outB_hi, void* outB_lo,
-                                            unsigned long long idx, float av, float v) {
+__device__ __forceinline__ void pack_store1(void* outS, void* outH, void* outL, unsigned long long idx, float c,
+                                            bool neg) {
   if constexpr (TF32) {
-    uint32_t ta, tb;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta) : "f"(av));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb) : "f"(v));
-    reinterpret_cast<uint32_t*>(outA_hi)[idx] = ta;
-    reinterpret_cast<uint32_t*>(outB_hi)[idx] = tb;
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(c));
+    reinterpret_cast<uint32_t*>(outH)[idx] = t;
+    if (outS) reinterpret_cast<uint32_t*>(outS)[idx] = t ^ (neg ? 0x80000000u : 0u);
   } else {
-    const __nv_bfloat16 ah = __float2bfloat16_rn(av);
-    const __nv_bfloat16 bh = __float2bfloat16_rn(v);
-    reinterpret_cast<__nv_bfloat16*>(outA_hi)[idx] = ah;
-    reinterpret_cast<__nv_bfloat16*>(outA_lo)[idx] = __float2bfloat16_rn(av - __bfloat162float(ah));
-    reinterpret_cast<__nv_bfloat16*>(outB_hi)[idx] = bh;
-    reinterpret_cast<__nv_bfloat16*>(outB_lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(bh));
+    const __nv_bfloat16 h = __float2bfloat16_rn(c);
+    const float hf = __bfloat162float(h);
+    reinterpret_cast<__nv_bfloat16*>(outH)[idx] = h;
+    reinterpret_cast<__nv_bfloat16*>(outL)[idx] = __float2bfloat16_rn(2.f * (c - hf));
+    if (outS) reinterpret_cast<__nv_bfloat16*>(outS)[idx] = __float2bfloat16_rn(flip(hf, neg));
   }
 }
 
@@ -418,22 +501,25 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
                                                        const int* __restrict__ slot,
                                                        const unsigned long long* __restrict__ lbase,
                                                        const unsigned long long* __restrict__ kp,
-                                                       void* __restrict__ outA_hi, void* __restrict__ outA_lo,
-                                                       void* __restrict__ outB_hi, void* __restrict__ outB_lo,
-                                                       unsigned int* err, long long timeout_cycles) {
+                                                       void* __restrict__ outS, void* __restrict__ outH,
+                                                       void* __restrict__ outL, unsigned int* err,
+                                                       long long timeout_cycles) {
   extern __shared__ __align__(16) float s_pack[];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ int s_abort;
   __shared__ unsigned long long s_lbase[kLmaxCap + 1], s_kp[kLmaxCap + 1];
   float* stage0 = s_pack;                                  // [kPackPrims][row], two stages
-  float* s_w = stage0 + 2 * kPackPrims * row;              // [kPackPrims]
+  float* s_w = stage0 + 2 * kPackPrims * row;              // [kPackPrims] sqrt|w|, sign bit = sign w
   int* s_slot = reinterpret_cast<int*>(s_w + kPackPrims);  // [(lmax+1)^2]
   const int nc = (lmax + 1) * (lmax + 1);
   const int64_t p0 = (int64_t)blockIdx.x * kPackPrims;
   const int pt = (int)min((int64_t)kPackPrims, np - p0);
   const uint32_t rowbytes = (uint32_t)row * 4u;
   for (int c = threadIdx.x; c < nc; c += blockDim.x) s_slot[c] = slot[c];
-  for (int q = threadIdx.x; q < pt; q += blockDim.x) s_w[q] = __ldg(wprim + p0 + q);
+  for (int q = threadIdx.x; q < pt; q += blockDim.x) {
+    const float wq = __ldg(wprim + p0 + q);
+    s_w[q] = copysignf(sqrtf(fabsf(wq)), wq);
+  }
   for (int l = threadIdx.x; l <= lmax; l += blockDim.x) {
     s_lbase[l] = lbase[l];
     s_kp[l] = kp[l];
@@ -463,8 +549,8 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
       const int tail = (int)(s_kp[l] - used);
       for (int e = threadIdx.x; e < nbins * tail; e += blockDim.x) {
         const int bb = e / tail, t = e - bb * tail;
-        pack_store1<TF32>(outA_hi, outA_lo, outB_hi, outB_lo,
-                          s_lbase[l] + (unsigned long long)bb * s_kp[l] + used + (unsigned long long)t, 0.f, 0.f);
+        pack_store1<TF32>(outS, outH, outL, op_index<TF32>(s_lbase[l], nbins, bb, used + (unsigned long long)t), 0.f,
+                          false);
       }
     }
   }
@@ -485,28 +571,31 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const float* __restrict__
         const int e0 = 8 * k - 16 * l * l;  // first element of the chunk in span l
         int q = e0 / nl;
         int mi = e0 - q * nl;
-        float v[8], av[8];
+        float cv[8];
+        bool ng[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          v[i] = rows[q * row + s_slot[l * l + mi]];
-          av[i] = s_w[q] * v[i];
+          const float sw = s_w[q];
+          cv[i] = fabsf(sw) * rows[q * row + s_slot[l * l + mi]];
+          ng[i] = signbit(sw);
           if (++mi == nl) {
             mi = 0;
             ++q;
           }
         }
-        const unsigned long long idx = s_lbase[l] + (unsigned long long)b * s_kp[l] +
-                                       (unsigned long long)p0 * nl + (unsigned long long)e0;
-        pack_store<TF32>(outA_hi, outA_lo, outB_hi, outB_lo, idx, av, v);
+        const unsigned long long idx =
+            op_index<TF32>(s_lbase[l], nbins, b, (unsigned long long)p0 * nl + (unsigned long long)e0);
+        pack_store<TF32>(outS, outH, outL, idx, cv, ng);
       }
     } else {
       for (int l = 0; l <= lmax; ++l) {
         const int nl = 2 * l + 1;
-        const unsigned long long base = s_lbase[l] + (unsigned long long)b * s_kp[l] + (unsigned long long)p0 * nl;
+        const unsigned long long k0 = (unsigned long long)p0 * nl;
         for (int e = threadIdx.x; e < pt * nl; e += blockDim.x) {
           const int q = e / nl, mi = e - q * nl;
-          const float v = rows[q * row + s_slot[l * l + mi]];
-          pack_store1<TF32>(outA_hi, outA_lo, outB_hi, outB_lo, base + (unsigned long long)e, s_w[q] * v, v);
+          const float sw = s_w[q];
+          pack_store1<TF32>(outS, outH, outL, op_index<TF32>(s_lbase[l], nbins, b, k0 + (unsigned long long)e),
+                            fabsf(sw) * rows[q * row + s_slot[l * l + mi]], signbit(sw));
         }
       }
     }
@@ -558,9 +647,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 int tc_npad(int nbins) { return std::max(16, (nbins + 15) / 16 * 16); }
 
-size_t tc_stage_bytes(bool tf32, int nbins) {
-  const size_t nA = tf32 ? 1 : 2;
-  return nA * (128 * 128 + (size_t)tc_npad(nbins) * 128);
+size_t tc_stage_bytes(bool tf32, bool signed_a, int nbins) {
+  return ((signed_a ? 1 : 0) + (tf32 ? 1 : 2)) * (size_t)tc_npad(nbins) * 128;
 }
 
 void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned long long>& lbase,
@@ -578,8 +666,8 @@ void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned 
 }
 
 cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row, int lmax,
-                        const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* ahi,
-                        void* alo, void* bhi, void* blo, unsigned int* err, cudaStream_t st) {
+                        const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* outS,
+                        void* outH, void* outL, unsigned int* err, cudaStream_t st) {
   if (np == 0) return cudaSuccess;
   const int64_t blocks = (np + kPackPrims - 1) / kPackPrims;
   const size_t smem = ((size_t)2 * kPackPrims * row + kPackPrims + (size_t)(lmax + 1) * (lmax + 1)) * 4;
@@ -587,31 +675,31 @@ cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t n
   if (tf32) {
     e = cudaFuncSetAttribute(k_pack<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_pack<true><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, ahi,
-                                                               alo, bhi, blo, err, kTcTimeoutCycles);
+    k_pack<true><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, outS,
+                                                               outH, outL, err, kTcTimeoutCycles);
   } else {
     e = cudaFuncSetAttribute(k_pack<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_pack<false><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, ahi,
-                                                                alo, bhi, blo, err, kTcTimeoutCycles);
+    k_pack<false><<<(unsigned)blocks, kPackThreads, smem, st>>>(M, wprim, np, nbins, row, lmax, slot, lbase, kp, outS,
+                                                                outH, outL, err, kTcTimeoutCycles);
   }
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const unsigned long long* h_lbase,
-                               const unsigned long long* h_kp, void* ahi, void* alo, void* bhi, void* blo,
-                               double* partial, int nsplit, unsigned int* err, bool inject_stall,
-                               cudaStream_t st) {
+                               const unsigned long long* h_kp, void* opA, void* opH, void* opL, double* partial,
+                               int nsplit, unsigned int* err, bool inject_stall, cudaStream_t st) {
   if (np == 0) return cudaSuccess;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   const int npad = tc_npad(nbins);
   const size_t esz = tf32 ? 4 : 2;
   const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  TcMaps maps;
-  std::memset(&maps, 0, sizeof(maps));
-  TcArgs a{};
+  TcArgsMaps am;
+  std::memset(&am, 0, sizeof(am));
+  TcMaps& maps = am.maps;
+  TcArgs& a = am.args;
   a.nl = lmax + 1;
   a.nbins = nbins;
   a.npad = npad;
@@ -621,38 +709,52 @@ cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const
   // about 2 s per wait; an injected stall gives up after about 10 ms
   a.timeout_cycles = inject_stall ? 20000000ll : kTcTimeoutCycles;
   a.inject_stall = inject_stall ? 1 : 0;
-  void* bases[4] = {ahi, alo, bhi, blo};
+  void* bases[3] = {opA, opH, opL};
+  a.signed_a = opA != opH ? 1 : 0;
+  a.cum[0] = 0;
   for (int l = 0; l <= lmax; ++l) {
-    a.ktiles[l] = (unsigned int)(h_kp[l] / (tf32 ? 32 : 64));
-    for (int k = 0; k < 4; ++k) {
-      if (tf32 && (k == 1 || k == 3)) continue;
+    a.cum[l + 1] = a.cum[l] + (unsigned int)(h_kp[l] / (tf32 ? 32 : 64));
+    for (int k = 0; k < 3; ++k) {
+      if ((tf32 && k == 2) || (k == 0 && !a.signed_a)) continue;
+      // [K tile][bin][128 bytes]: a box is one K tile of npad rows (rows past
+      // nbins zero-filled)
       void* gaddr = static_cast<char*>(bases[k]) + h_lbase[l] * esz;
-      cuuint64_t gdim[2] = {(cuuint64_t)h_kp[l], (cuuint64_t)nbins};
-      cuuint64_t gstride[1] = {(cuuint64_t)(h_kp[l] * esz)};
-      cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)(k < 2 ? 128 : npad)};
-      cuuint32_t estr[2] = {1, 1};
-      CUresult r = enc(&maps.m[l][k], dt, 2, gaddr, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      const cuuint64_t kt = 128 / esz;
+      cuuint64_t gdim[3] = {kt, (cuuint64_t)nbins, (cuuint64_t)(h_kp[l] / kt)};
+      cuuint64_t gstride[2] = {128, (cuuint64_t)nbins * 128};
+      cuuint32_t box[3] = {(cuuint32_t)kt, (cuuint32_t)npad, 1};
+      cuuint32_t estr[3] = {1, 1, 1};
+      CUresult r = enc(&maps.m[l][k], dt, 3, gaddr, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
   }
-  const size_t stage = tc_stage_bytes(tf32, nbins);
+  const size_t stage = tc_stage_bytes(tf32, a.signed_a != 0, nbins);
+  const size_t slack = (size_t)kTcM * 128;  // the A view's overrun past the last stage
   const size_t budget = 220 * 1024;
-  a.stages = (int)std::max<size_t>(2, std::min<size_t>(8, (budget - 1024 - 256) / stage));
+  a.stages = (int)std::max<size_t>(2, std::min<size_t>(16, (budget - 1024 - slack - 256) / stage));
+  // accumulators: 2 flush buffers x 2 chains x N columns
+  a.ncol_d = tf32 ? npad : 2 * npad;
   int ncols = 32;
-  while (ncols < 2 * npad) ncols *= 2;
+  while (ncols < 4 * a.ncol_d) ncols *= 2;
   a.ncols = ncols;
-  const size_t smem = 1024 + a.stages * stage + 256;
+  const size_t smem = 1024 + a.stages * stage + slack + 256;
+  // one wave: one CTA per SM (the shared-memory ring takes the SM), at most
+  // one per partial row
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidValue;
+  const int grid = std::max(1, std::min(nsm, nsplit));
   cudaError_t e;
   if (tf32) {
     e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_contract_tc<true><<<dim3(nsplit, lmax + 1), kTcThreads, smem, st>>>(maps, a);
+    k_contract_tc<true><<<grid, kTcThreads, smem, st>>>(am);
   } else {
     e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_contract_tc<false><<<dim3(nsplit, lmax + 1), kTcThreads, smem, st>>>(maps, a);
+    k_contract_tc<false><<<grid, kTcThreads, smem, st>>>(am);
   }
   ++g_launches;
   return cudaGetLastError();

@@ -356,13 +356,14 @@ int tc_npad(int nbins);
 void tc_layout(bool tf32, int64_t np, int nbins, int lmax, std::vector<unsigned long long>& lbase,
                std::vector<unsigned long long>& kp, size_t* elems);
 // slot: the layout's slot of coefficient l*l+l+m (l <= lmax)
+// outS (sign(w) times the scaled coefficients) may be NULL: no negative weights
 cudaError_t launch_pack(bool tf32, const float* M, const float* wprim, int64_t np, int nbins, int row, int lmax,
-                        const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* ahi,
-                        void* alo, void* bhi, void* blo, unsigned int* err, cudaStream_t st);
+                        const int* slot, const unsigned long long* lbase, const unsigned long long* kp, void* outS,
+                        void* outH, void* outL, unsigned int* err, cudaStream_t st);
+// opA = outS, or outH when there is no negative weight
 cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const unsigned long long* h_lbase,
-                               const unsigned long long* h_kp, void* ahi, void* alo, void* bhi, void* blo,
-                               double* partial, int nsplit, unsigned int* err, bool inject_stall,
-                               cudaStream_t st);
+                               const unsigned long long* h_kp, void* opA, void* opH, void* opL, double* partial,
+                               int nsplit, unsigned int* err, bool inject_stall, cudaStream_t st);
 cudaError_t launch_finalize_tc(const double* partial, int lmax, int nsplit, int nbins, double* zeta,
                                cudaStream_t st);
 

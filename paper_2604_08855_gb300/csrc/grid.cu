@@ -18,9 +18,11 @@ __global__ void k_ingest(const double* __restrict__ xyz, const double* __restric
                          uint32_t key_base, uint32_t val_base, uint32_t* __restrict__ key,
                          uint32_t* __restrict__ val, uint4* __restrict__ pts, uint32_t* flags) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int neg = 0;  // a negative weight in this thread's points
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double p[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
     double wi = w ? w[i] : 1.0;
+    neg |= wi < 0.0;
     bool bad = !isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2]) || !isfinite(wi);
     if (bad) {
       atomicOr(flags, 1u);
@@ -50,6 +52,8 @@ __global__ void k_ingest(const double* __restrict__ xyz, const double* __restric
     val[i] = val_base + (uint32_t)i;
     pts[i] = make_uint4(u[0], u[1], u[2], __float_as_uint((float)wi));
   }
+  // flags[3]: the catalogue has a negative weight (one vote per block)
+  if (__syncthreads_or(neg) && threadIdx.x == 0) atomicOr(flags + 3, 1u);
 }
 
 cudaError_t launch_ingest(const double* xyz, const double* w, int64_t n, double box,
