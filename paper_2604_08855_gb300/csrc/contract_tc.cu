@@ -20,7 +20,8 @@
 // 16-element K step: its A view starts at the stage's first tile and runs 64
 // rows on into the next tiles (or the ring's slack), so rows past npad of D
 // are products of other rows and are ignored.  The K steps of a tile
-// alternate between two accumulators.  FP32 accumulation happens in TMEM;
+// alternate between two accumulators (one when TMEM is short: 64 bins).
+// Two CTAs share an SM.  FP32 accumulation happens in TMEM;
 // every kTcFlushTiles K tiles the accumulators are drained to FP64 registers
 // (double buffered in TMEM so the MMA issue never waits for the drain), and
 // the FP64 totals go to a per-CTA partial that a fixed-order FP64 reduction
@@ -51,6 +52,10 @@ namespace ctb {
 
 constexpr int kTcThreads = 192;
 constexpr int kTcFlushTiles = 64;
+// CTAs resident per SM, each with its own TMA pipeline (shared memory and
+// TMEM split between them): one CTA's ring of 16 stages kept the loads
+// latency-bound at about 2.5 TB/s; two per SM doubled the throughput
+constexpr int kTcCtasPerSm = 2;
 constexpr long long kTcTimeoutCycles = 4000000000ll;  // about 2 s
 
 struct TcMaps {
@@ -65,6 +70,7 @@ struct TcArgs {
   int stages;
   int ncols;                          // TMEM columns allocated
   int ncol_d;                         // columns of one accumulator (the MMA's N)
+  int nchain;                         // accumulator chains the K steps of a tile take in turn (1 or 2)
   unsigned int cum[kLmaxCap + 2];     // 128-byte K tiles of the l before l (cum[nl] = all)
   double* partial;                    // [nl][nsplit][nbins][nbins]
   unsigned int* err;                  // bit 0: a bounded wait timed out
@@ -197,8 +203,8 @@ __host__ __device__ constexpr uint32_t make_idesc(bool tf32, int n) {
 // contraction kernel: gridDim.x CTAs, each a contiguous range of the
 // concatenated (l, K tile) sequence; partial row blockIdx.x of each l
 
-template <bool TF32>
-__global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_constant__ TcArgsMaps am) {
+template <bool TF32, int NCH>
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_contract_tc(const __grid_constant__ TcArgsMaps am) {
   const TcMaps& maps = am.maps;
   const TcArgs& a = am.args;
   extern __shared__ uint8_t s_raw[];
@@ -315,12 +321,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
           tc_fence_after();
           const uint32_t sa = smem_u32(sm + (size_t)s * STAGE);
           const uint32_t b_hi = sa + A_BYTES;
-          // two accumulator chains (the even and odd 16-element K steps)
+          // NCH accumulator chains (the 16-element K steps in turn)
+          constexpr uint32_t nch = NCH;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t acc0 = (first_of_flush && kk < 2) ? 0u : 1u;
+            const uint32_t acc0 = (first_of_flush && (uint32_t)kk < nch) ? 0u : 1u;
             const uint32_t ko = (uint32_t)kk * 32u;  // 32 bytes of K per MMA
-            const uint32_t d = taddr + (buf * 2u + (uint32_t)(kk & 1)) * (uint32_t)a.ncol_d;
+            const uint32_t d = taddr + (buf * nch + (uint32_t)kk % nch) * (uint32_t)a.ncol_d;
             tc_mma<TF32>(d, sw128_desc(sa + ko), sw128_desc(b_hi + ko), idesc, acc0);
           }
           tc_commit(empty + s);
@@ -361,20 +368,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           if (c * 8 < a.npad) {
-            // Z[r][col] = the two chains' S H^T plus their S L2^T (BF16)
-            const uint32_t col = buf * 2u * (uint32_t)a.ncol_d + (uint32_t)(c * 8);
+            // Z[r][col] = the chains' S H^T plus their S L2^T (BF16)
+            const uint32_t col = buf * (uint32_t)NCH * (uint32_t)a.ncol_d + (uint32_t)(c * 8);
             float v[8], u[8];
             tmem_ld8(row_addr + col, v);
-            tmem_ld8(row_addr + col + (uint32_t)a.ncol_d, u);
+            if constexpr (NCH > 1) {
+              tmem_ld8(row_addr + col + (uint32_t)a.ncol_d, u);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] += u[q];
+              for (int q = 0; q < 8; ++q) v[q] += u[q];
+            }
             if (!TF32) {
               tmem_ld8(row_addr + col + (uint32_t)a.npad, u);
 #pragma unroll
               for (int q = 0; q < 8; ++q) v[q] += u[q];
-              tmem_ld8(row_addr + col + (uint32_t)a.ncol_d + (uint32_t)a.npad, u);
+              if constexpr (NCH > 1) {
+                tmem_ld8(row_addr + col + (uint32_t)a.ncol_d + (uint32_t)a.npad, u);
 #pragma unroll
-              for (int q = 0; q < 8; ++q) v[q] += u[q];
+                for (int q = 0; q < 8; ++q) v[q] += u[q];
+              }
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc[c * 8 + q] += (double)v[q];
@@ -732,30 +743,26 @@ cudaError_t launch_contract_tc(bool tf32, int64_t np, int nbins, int lmax, const
   }
   const size_t stage = tc_stage_bytes(tf32, a.signed_a != 0, nbins);
   const size_t slack = (size_t)kTcM * 128;  // the A view's overrun past the last stage
-  const size_t budget = 220 * 1024;
+  const size_t budget = (220 * 1024) / kTcCtasPerSm;
   a.stages = (int)std::max<size_t>(2, std::min<size_t>(16, (budget - 1024 - slack - 256) / stage));
-  // accumulators: 2 flush buffers x 2 chains x N columns
+  // accumulators: 2 flush buffers x nchain chains x N columns, within this
+  // CTA's share of the SM's 512 TMEM columns
   a.ncol_d = tf32 ? npad : 2 * npad;
+  a.nchain = 2 * 2 * a.ncol_d * kTcCtasPerSm <= 512 ? 2 : 1;
   int ncols = 32;
-  while (ncols < 4 * a.ncol_d) ncols *= 2;
+  while (ncols < 2 * a.nchain * a.ncol_d) ncols *= 2;
   a.ncols = ncols;
   const size_t smem = 1024 + a.stages * stage + slack + 256;
-  // one wave: one CTA per SM (the shared-memory ring takes the SM), at most
-  // one per partial row
+  // one wave: kTcCtasPerSm CTAs per SM, at most one per partial row
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return cudaErrorInvalidValue;
-  const int grid = std::max(1, std::min(nsm, nsplit));
-  cudaError_t e;
-  if (tf32) {
-    e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_contract_tc<true><<<grid, kTcThreads, smem, st>>>(am);
-  } else {
-    e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_contract_tc<false><<<grid, kTcThreads, smem, st>>>(am);
-  }
+  const int grid = std::max(1, std::min(kTcCtasPerSm * nsm, nsplit));
+  void (*fn)(const TcArgsMaps) = tf32 ? (a.nchain == 2 ? k_contract_tc<true, 2> : k_contract_tc<true, 1>)
+                                     : (a.nchain == 2 ? k_contract_tc<false, 2> : k_contract_tc<false, 1>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, kTcThreads, smem, st>>>(am);
   ++g_launches;
   return cudaGetLastError();
 }
