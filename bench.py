@@ -462,8 +462,10 @@ def run_ours(args):
     est.set_stream(stream)
     if args.cells_per_rmax:
         est.set_option(ctb.OPT_CELLS_PER_RMAX, args.cells_per_rmax)
-    elif not batch:
-        est.set_option(ctb.OPT_AUTOTUNE, 1)  # tuned on the first set_points (a warm-up step)
+    else:
+        # tuned on the first set_points or batch (a warm-up step); a batch
+        # tunes on its largest catalogue
+        est.set_option(ctb.OPT_AUTOTUNE, 1)
     if batch:
         d_cats = [(torch.from_numpy(x).to(dev), torch.from_numpy(v).to(dev)) for x, v in zip(xyz, w)]
         d_zeta = torch.zeros((len(xyz),) + est.zeta_shape, dtype=torch.float64, device=dev)
@@ -682,8 +684,8 @@ def run_ours(args):
                                       "tf32": "FP32 pair kernel, TF32 tcgen05 contraction with FP32 accumulate, "
                                               "FP64 reduce"}[headline],
                    **({"batch_mode": args.batch_mode} if batch else {}),
-                   "cells_per_rmax": args.cells_per_rmax or 8 if batch else est.grid()[0],
-                   "grid": "fixed" if args.cells_per_rmax or batch else "autotuned",
+                   "cells_per_rmax": est.grid()[0],
+                   "grid": "fixed" if args.cells_per_rmax else "autotuned",
                    "l2": "flushed (256 MB write) before every step",
                    "inputs": "device-resident float64 xyz, w",
                    **({"parallelism": f"primaries sharded over {world} GPUs, one FP64 all-reduce of zeta"}

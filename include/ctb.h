@@ -226,7 +226,9 @@ int ctb_get_alm(ctb_ctx* ctx, const int64_t* primary_idx, int64_t m, float* alm_
  * All catalogues go into one sorted grid (cell key = catalogue * cells +
  * cell), one pair pipeline runs over every primary with each neighbour search
  * kept inside its own catalogue, and the contraction keeps one set of FP64
- * partial sums per catalogue.  The batch replaces the context's catalogue:
+ * partial sums per catalogue.  With CTB_OPT_AUTOTUNE set (and no fixed
+ * CTB_OPT_CELLS_PER_RMAX) the first batch tunes the grid on its largest
+ * catalogue and the context keeps it.  The batch replaces the context's catalogue:
  * call ctb_set_points again before the next ctb_compute.  Periodic boxes only.
  * Errors: CTB_ERR_ARG (k < 1, a NULL xyz[i] with n[i] > 0, a negative n[i],
  * more than 2^31 points in total or k * grid cells >= 2^32),
@@ -322,9 +324,10 @@ int ctb_get_2pcf(ctb_ctx* ctx, double* out, int cap);
  */
 int ctb_edge_correct(ctb_ctx* ctx, const double* zeta_nnn, const double* zeta_rrr, double* zeta_out);
 
-/* The cell grid of the current catalogue: cells per r_max along an axis (the
- * option, else the autotuner's choice, else 8) and cells per axis of the
- * (per-catalogue) cube.  CTB_ERR_STATE before ctb_set_points. */
+/* The cell grid of the current catalogue (or of the last ctb_compute_batch):
+ * cells per r_max along an axis (the option, else the autotuner's choice,
+ * else 8) and cells per axis of the (per-catalogue) cube.  CTB_ERR_STATE
+ * before ctb_set_points or a batch. */
 int ctb_get_grid(ctb_ctx* ctx, int* cells_per_rmax, int* cells_per_axis);
 
 /*

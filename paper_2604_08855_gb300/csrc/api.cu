@@ -52,6 +52,7 @@ struct ctb_ctx {
   // catalogue
   int64_t n = -1;
   bool negw = true;  // the catalogue has a negative weight (from the ingest)
+  bool batch_grid = false;  // c->g is the grid of the last batch (c->n < 0 then)
   Geom g{};
   double unit = 0;
   double origin[3] = {0, 0, 0};
@@ -924,6 +925,7 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   if (r) return r;
   c->n = -1;
   c->batch_keys = nullptr;
+  c->batch_grid = false;
   // grid of one periodic catalogue
   const int cpr = grid_cells_per_rmax(c);
   Geom g{};
@@ -1047,6 +1049,7 @@ int batch_impl(ctb_ctx* c, const double* const* xyz, const double* const* w, con
   if (tc_err) return fail(c, CTB_ERR_TIMEOUT, "tensor-core contraction: a bounded wait timed out");
   c->pairsum_segs = k;
   c->pairsum_parts = pl.nparts;
+  c->batch_grid = true;
   return CTB_OK;
 }
 
@@ -1401,6 +1404,21 @@ int ctb_get_alm(ctb_ctx* c, const int64_t* primary_idx, int64_t m, float* alm_ou
 int ctb_compute_batch(ctb_ctx* c, const double* const* xyz, const double* const* w, const int64_t* n, int k,
                       double* zeta_out) {
   if (!c) return CTB_ERR_ARG;
+  // the autotuner's grid: tuned once, on the batch's largest catalogue (the
+  // one with the most work), and kept for the context
+  if (c->autotune && c->cells_per_rmax == 0 && c->tuned_cpr == 0 && k >= 1 && xyz && n && c->periodic &&
+      !c->sphere) {
+    int imax = 0;
+    for (int i = 1; i < k; ++i)
+      if (n[i] > n[imax]) imax = i;
+    if (n[imax] > 1 && xyz[imax]) {
+      int r = autotune_grid(c, xyz[imax], (w && w[imax]) ? w[imax] : nullptr, n[imax]);
+      if (r) {
+        c->tuned_cpr = 0;
+        return r;
+      }
+    }
+  }
   const unsigned long long l0 = g_launches;
   int r = batch_impl(c, xyz, w, n, k, zeta_out);
   c->launches_points = 0;
@@ -1538,7 +1556,7 @@ int ctb_get_2pcf(ctb_ctx* c, double* out, int cap) {
 
 int ctb_get_grid(ctb_ctx* c, int* cells_per_rmax, int* cells_per_axis) {
   if (!c || !cells_per_rmax || !cells_per_axis) return CTB_ERR_ARG;
-  if (c->n < 0) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
+  if (c->n < 0 && !c->batch_grid) return fail(c, CTB_ERR_STATE, "no catalogue: call ctb_set_points first");
   *cells_per_rmax = grid_cells_per_rmax(c);
   *cells_per_axis = (int)c->g.nc;
   return CTB_OK;
