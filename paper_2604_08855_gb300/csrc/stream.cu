@@ -241,6 +241,62 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
         // grows the buffer and counts the chunk again
         codes_ok = pos + span <= a.code_cap;
       }
+      if constexpr (FILL) {
+        // The row block's codes are one contiguous run: lane t's segments
+        // in order, each padded to 4 codes.  Walk it as a stream, lane l
+        // taking code word k0 + l (4 candidates of one segment), with the
+        // next step's word loaded ahead.
+        const uint32_t len0 = s0 < e0 ? (e0 - s0 + 3u) & ~3u : 0u;
+        const uint32_t len1 = s1 < e1 ? (e1 - s1 + 3u) & ~3u : 0u;
+        uint32_t incl = len0 + len1;  // inclusive prefix of the padded lengths over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const uint32_t excl = incl - len0 - len1;
+        const uint32_t nwords = (uint32_t)(span >> 2);
+        const uint32_t* rbw = reinterpret_cast<const uint32_t*>(a.codes + pos);
+        uint32_t word = (uint32_t)lane < nwords ? __ldcs(rbw + lane) : 0xffffffffu;
+        for (uint32_t k0 = 0; k0 < nwords; k0 += 32) {
+          const uint32_t kn = k0 + 32u + (uint32_t)lane;
+          const uint32_t wnext = kn < nwords ? __ldcs(rbw + kn) : 0xffffffffu;
+          // the segment of code 4 (k0 + lane): first lane t with incl_t above it
+          const uint32_t cpos = 4u * (k0 + (uint32_t)lane);
+          int t = 0;
+#pragma unroll
+          for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(0xffffffffu, incl, t + st - 1) <= cpos) t += st;
+          const uint32_t r = cpos - __shfl_sync(0xffffffffu, excl, t);
+          const uint32_t l0 = __shfl_sync(0xffffffffu, len0, t);
+          const uint32_t sa0 = __shfl_sync(0xffffffffu, s0, t), ea0 = __shfl_sync(0xffffffffu, e0, t);
+          const uint32_t sa1 = __shfl_sync(0xffffffffu, s1, t), ea1 = __shfl_sync(0xffffffffu, e1, t);
+          const bool first = r < l0;
+          const uint32_t jb = first ? sa0 + r : sa1 + (r - l0);
+          const uint32_t je = first ? ea0 : ea1;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t j = jb + (uint32_t)k;
+            const uint32_t code = (word >> (8 * k)) & 0xffu;
+            // words past the run read as all kNoBin; the padding after a
+            // segment's end holds no codes
+            const bool inb = code != kNoBin && j < je;
+            const int b = (int)code;
+            const unsigned act = __ballot_sync(0xffffffffu, inb);
+            if (inb) {
+              const unsigned grp = __match_any_sync(act, b);
+              const unsigned rank = __popc(grp & lt);
+              const uint32_t c0 = cnt[b];
+              __syncwarp(act);
+              __stcs(a.lists + ((uint64_t)c0 + rank), j);
+              if (rank == 0) cnt[b] = c0 + __popc(grp);
+            }
+            __syncwarp();
+          }
+          word = wnext;
+        }
+        continue;
+      }
       unsigned pend = __ballot_sync(0xffffffffu, s0 < e0 || s1 < e1);
       while (pend) {
         // ---- next segment (warp-uniform)
@@ -255,77 +311,51 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(StreamArgs a) {
         pend = __ballot_sync(0xffffffffu, s0 < e0 || s1 < e1);
         const unsigned long long seg0 = pos;  // code of candidate j: codes[seg0 + (j - cs)]
         pos += (ce - cs + 3u) & ~3u;
-        if (FILL) {
-          // 128 candidates per step: lane l takes candidates 4l .. 4l+3 of it
-          const uint32_t* segw = reinterpret_cast<const uint32_t*>(a.codes + seg0);
-          for (uint32_t base = cs; base < ce; base += 128) {
-            const uint32_t j4 = base + 4u * (uint32_t)lane;
-            const uint32_t word = j4 < ce ? __ldcs(segw + ((j4 - cs) >> 2)) : 0xffffffffu;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint32_t j = j4 + (uint32_t)k;
-              const uint32_t code = (word >> (8 * k)) & 0xffu;
-              const bool inb = j < ce && code != kNoBin;
-              const int b = (int)code;
-              const unsigned act = __ballot_sync(0xffffffffu, inb);
-              if (inb) {
-                const unsigned grp = __match_any_sync(act, b);
-                const unsigned rank = __popc(grp & lt);
-                const uint32_t c0 = cnt[b];
-                __syncwarp(act);
-                __stcs(a.lists + ((uint64_t)c0 + rank), j);
-                if (rank == 0) cnt[b] = c0 + __popc(grp);
-              }
-              __syncwarp();
+        for (uint32_t base = cs; base < ce; base += 32) {
+          const uint32_t j = base + lane;
+          const bool valid = j < ce;
+          // lanes past the segment load its last point and are masked by `valid`
+          const uint4 q = __ldg(a.pts + (valid ? j : ce - 1u));
+          const int ix = (int)(q.x - P.x), iy = (int)(q.y - P.y), iz = (int)(q.z - P.z);
+          const float dx = __int2float_rn(ix), dy = __int2float_rn(iy), dz = __int2float_rn(iz);
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          // rlo2_u > 0 also excludes r = 0 (coincident points)
+          bool inb = valid && r2 >= g.rlo2_u && r2 < g.rhi2_u;
+          int b = 0;
+          if (inb) {
+            const float r = r2 * rsqrtf(r2);
+            float tt, guard;
+            if constexpr (GEN) {
+              // sphere: the bin of theta = 2 asin(chord / 2).  Its float
+              // error stays below 1e-6 theta while chord / 2 <= 0.99 (asin
+              // is ill-conditioned towards 1); the guard is ten times that,
+              // and larger chords always take the exact test.
+              const float x = r * g.half_unit;
+              const float th = 2.f * asinf(fminf(x, 1.f));
+              tt = (th - g.tmin) * g.inv_dt;
+              guard = x > 0.99f ? 1.f : fmaxf(1e-4f, fmaf(1e-5f, th, 1e-7f) * g.inv_dt);
+            } else {
+              tt = (r - g.rmin_u) * g.inv_dr_u;
+              guard = 1e-4f;
             }
-          }
-        } else {
-          for (uint32_t base = cs; base < ce; base += 32) {
-            const uint32_t j = base + lane;
-            const bool valid = j < ce;
-            // lanes past the segment load its last point and are masked by `valid`
-            const uint4 q = __ldg(a.pts + (valid ? j : ce - 1u));
-            const int ix = (int)(q.x - P.x), iy = (int)(q.y - P.y), iz = (int)(q.z - P.z);
-            const float dx = __int2float_rn(ix), dy = __int2float_rn(iy), dz = __int2float_rn(iz);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            // rlo2_u > 0 also excludes r = 0 (coincident points)
-            bool inb = valid && r2 >= g.rlo2_u && r2 < g.rhi2_u;
-            int b = 0;
-            if (inb) {
-              const float r = r2 * rsqrtf(r2);
-              float tt, guard;
-              if constexpr (GEN) {
-                // sphere: the bin of theta = 2 asin(chord / 2).  Its float
-                // error stays below 1e-6 theta while chord / 2 <= 0.99 (asin
-                // is ill-conditioned towards 1); the guard is ten times that,
-                // and larger chords always take the exact test.
-                const float x = r * g.half_unit;
-                const float th = 2.f * asinf(fminf(x, 1.f));
-                tt = (th - g.tmin) * g.inv_dt;
-                guard = x > 0.99f ? 1.f : fmaxf(1e-4f, fmaf(1e-5f, th, 1e-7f) * g.inv_dt);
+            b = (int)floorf(tt);
+            const float fr = tt - (float)b;
+            if ((unsigned)b >= (unsigned)nbins || fabsf(fr - 0.5f) > 0.5f - guard) {
+              // within float rounding of an edge: exact integer r^2 vs
+              // exact thresholds
+              const unsigned long long e2 = (unsigned long long)((long long)ix * ix + (long long)iy * iy +
+                                                                 (long long)iz * iz);
+              if (e2 == 0ull || e2 < __ldg(a.thr) || e2 >= __ldg(a.thr + nbins)) {
+                inb = false;
               } else {
-                tt = (r - g.rmin_u) * g.inv_dr_u;
-                guard = 1e-4f;
-              }
-              b = (int)floorf(tt);
-              const float fr = tt - (float)b;
-              if ((unsigned)b >= (unsigned)nbins || fabsf(fr - 0.5f) > 0.5f - guard) {
-                // within float rounding of an edge: exact integer r^2 vs
-                // exact thresholds
-                const unsigned long long e2 = (unsigned long long)((long long)ix * ix + (long long)iy * iy +
-                                                                   (long long)iz * iz);
-                if (e2 == 0ull || e2 < __ldg(a.thr) || e2 >= __ldg(a.thr + nbins)) {
-                  inb = false;
-                } else {
-                  b = min(max(b, 0), nbins - 1);
-                  while (e2 < __ldg(a.thr + b)) --b;
-                  while (e2 >= __ldg(a.thr + b + 1)) ++b;
-                }
+                b = min(max(b, 0), nbins - 1);
+                while (e2 < __ldg(a.thr + b)) --b;
+                while (e2 >= __ldg(a.thr + b + 1)) ++b;
               }
             }
-            if (valid && codes_ok) __stcs(a.codes + (seg0 + (j - cs)), inb ? (unsigned char)b : (unsigned char)kNoBin);
-            if (inb) cnt[b * 32 + lane] += 1u;  // lane-private: no ordering, no conflict
           }
+          if (valid && codes_ok) __stcs(a.codes + (seg0 + (j - cs)), inb ? (unsigned char)b : (unsigned char)kNoBin);
+          if (inb) cnt[b * 32 + lane] += 1u;  // lane-private: no ordering, no conflict
         }
       }
     }

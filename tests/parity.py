@@ -20,16 +20,21 @@ def zeta_err(z, ref):
     return float(np.max(diff / s))
 
 
-def alm_err(a, a_ref, w2_sum, lmax):
-    """|a - a_ref| / sqrt((2l+1)/(4 pi) sum_{j in b} w_j^2) per (p, b, l, m), max.
+def alm_err(a, a_ref, w1_sum, lmax):
+    """|a - a_ref| / (sqrt((2l+1)/(4 pi)) sum_{j in b} |w_j|) per (p, b, l, m), max.
 
-    w2_sum[p, b] = sum of squared secondary weights in the bin: the natural
-    scale of a sum of |w_j| sqrt((2l+1)/4pi)-bounded terms with random signs.
+    w1_sum[p, b] = sum of |w_j| over the bin's secondaries, so the scale is
+    the bound on every term's magnitude summed: the scale of the forward
+    error of a floating-point sum (sum |terms| times the unit roundoff and
+    the evaluation's conditioning).  A root-sum-square scale would assume
+    that rounding errors cancel at random; the moments of a factored
+    polynomial basis do not guarantee that (their conversion to a_lm
+    cancels, by up to a few tens at l = 10).
     """
     err = 0.0
     for l in range(lmax + 1):
         sl = slice(l * l, (l + 1) ** 2)
-        scale = np.sqrt((2 * l + 1) / (4 * np.pi) * w2_sum)[:, :, None]
+        scale = (np.sqrt((2 * l + 1) / (4 * np.pi)) * w1_sum)[:, :, None]
         diff = np.abs(np.asarray(a[:, :, sl], dtype=np.float64) - a_ref[:, :, sl])
         ok = scale > 0
         assert np.all(diff[~np.broadcast_to(ok, diff.shape)] < 1e-30)
