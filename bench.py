@@ -104,7 +104,7 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-PASS_CAP = 136          # accumulators per pass of the accumulation kernel
+PASS_CAP = 184          # accumulators per pass of the accumulation kernel
 SINGLE_PASS_LMAX = 10   # up to here one pass holds every coefficient
 FIRST_PASS_M1 = 2       # above it the first (Chebyshev) pass ends at m = 2
 

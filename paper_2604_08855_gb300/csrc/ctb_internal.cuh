@@ -25,8 +25,10 @@ constexpr int kLmaxCap = CTB_LMAX_CAP;
 constexpr size_t kListSlackBytes = 1024;
 constexpr int kNbinsCap = CTB_NBINS_CAP;
 constexpr int kWarp = 32;
-// coefficients accumulated per pass of the pair kernel (register budget)
-constexpr int kPassCap = 136;
+// coefficients accumulated per pass of the pair kernel (register budget: a
+// pass of more than 136 runs at 255 registers and 8 warps per SM, which
+// measured faster at l_max 20 than one more pass at 168 registers and 12)
+constexpr int kPassCap = 184;
 
 // ---------------------------------------------------------------------------
 // grid / estimator geometry shared by the kernels

@@ -471,9 +471,9 @@ __host__ __device__ constexpr size_t alm_table_bytes(int L, int P) {
 }
 
 // resident blocks of 4 warps the register budget of a pass is sized for
-// (each of the SM's four schedulers holds a quarter of the registers: 3
-// warps per scheduler allow 168 registers a thread, 4 allow 128)
-__host__ __device__ constexpr int alm_min_blocks(int ncp) { return ncp <= 32 ? 5 : (ncp <= 64 ? 4 : 3); }
+// (each of the SM's four schedulers holds a quarter of the registers: 2
+// warps per scheduler allow 255 registers a thread, 3 allow 168, 4 allow 128)
+__host__ __device__ constexpr int alm_min_blocks(int ncp) { return ncp <= 32 ? 5 : (ncp <= 64 ? 4 : (ncp <= 136 ? 3 : 2)); }
 
 // per warp: the flush's transpose buffer, the slot totals, then the
 // primary's list offsets and counts

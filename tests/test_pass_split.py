@@ -55,4 +55,4 @@ def test_bench_pass_split_matches_library(tmp_path):
     for L, passes in lib.items():
         assert bench.pass_split(L) == passes, L
     assert lib[10] == [(0, 10)]
-    assert lib[20] == [(0, 2), (3, 5), (6, 10), (11, 20)]
+    assert lib[20] == [(0, 2), (3, 7), (8, 20)]
