@@ -53,9 +53,10 @@ SM_COUNT = 152
 INST_PER_UPDATE = 2.6
 # DRAM bytes per pair of the accumulation kernel from one ncu capture of the
 # current k_alm (dram__bytes_read.sum + dram__bytes_write.sum over the pairs of
-# the captured launch).
-# Keyed by l_max; a missing entry reports null traffic.
-K_ALM_DRAM_BYTES_PER_PAIR = {10: 4.395}
+# the captured launches, summed over the m-pass launches of one chunk: one at
+# l_max 10, three at l_max 20).  Keyed by l_max; a missing entry reports null
+# traffic.
+K_ALM_DRAM_BYTES_PER_PAIR = {10: 4.385, 20: 21.17}
 FP32_LANES_PER_SM = 128
 
 
@@ -190,30 +191,53 @@ def flops_per_pair(lmax: int) -> int:
 
 
 def traffic_per_launch(lmax: int, npairs: int, chunks: int):
-    """DRAM bytes of one mean k_alm launch of this run, scaled from the
-    captured launch by its pairs (the traffic is the list words, which grow
-    with the pairs), or None when no capture of the current kernel exists."""
+    """DRAM bytes of one mean k_alm launch of this run (a chunk runs one
+    launch per m-pass), scaled from the captured launches by their pairs (the
+    traffic is the list words and the gathers' misses, which grow with the
+    pairs), or None when no capture of the current kernel exists."""
     per_pair = K_ALM_DRAM_BYTES_PER_PAIR.get(lmax)
     if per_pair is None or chunks <= 0:
         return None
-    return per_pair * npairs / chunks
+    return per_pair * npairs / (chunks * len(pass_split(lmax)))
 
 
-def contraction_roofline(prec, kw, stages_ms, pk, pk_kind, npts):
-    """Tensor-pipe roofline of the tcgen05 contraction (mixed precisions only):
-    2 * primaries * (l_max+1)^2 * nbins^2 FLOPs per step (x3 for the BF16 hi/lo
-    split) over the contraction stage's event time, against the measured dense
-    BF16 peak (TF32: x 1.1/2.25, the nominal TF32/BF16 ratio)."""
+def contraction_roofline(prec, kw, stages_ms, pk, pk_kind, npts, negw):
+    """Roofline of the tcgen05 contraction (mixed precisions only).  It reads
+    each operand element once, at about 48 FLOP per byte for BF16x3 against a
+    machine balance near 290, so it is bound by HBM: the algorithmic bytes
+    are the operand tensors (BF16x3: H and 2L, plus sign(w) H when a weight is
+    negative, 2 bytes an element; TF32: H, plus sign(w) H, 4 bytes), primaries
+    x nbins x (l_max+1)^2 elements each, over the contraction stage's event
+    time against the measured copy bandwidth.  The tensor-pipe rate (2 x
+    primaries x (l_max+1)^2 x nbins^2 FLOPs, x3 for the BF16 hi/lo split,
+    against the measured dense BF16 peak; TF32 x 1.1/2.25) and the pack
+    stage's HBM rate (reads the FP32 coefficient, writes the operand
+    elements) ride along."""
     if prec == "fp32" or kw.get("sphere") or stages_ms.get("contraction", 0.0) <= 0.0:
         return {}
     nc = ncoef(kw)
+    elems = float(npts) * nc * kw["nbins"]
+    if prec == "bf16x3":
+        op_bytes = elems * 2.0 * (3 if negw else 2)
+    else:
+        op_bytes = elems * 4.0 * (2 if negw else 1)
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    t = stages_ms["contraction"] / 1e3
+    achieved = op_bytes / t / 1e9
     flops = 2.0 * npts * nc * kw["nbins"] ** 2 * (3 if prec == "bf16x3" else 1)
-    peak = float(pk.get("bf16_tflops", 1900.0)) * (1.0 if prec == "bf16x3" else 1.1 / 2.25)
-    achieved = flops / (stages_ms["contraction"] / 1e3) / 1e12
-    return {"roofline_contraction": {"bound": "tensor", "kernel": "k_contract_tc", "achieved": achieved,
-                                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                                     "peak_note": f"dense BF16 ({pk_kind}, burst)"
-                                                  + (" x 1.1/2.25 for TF32" if prec == "tf32" else "")}}
+    peak_tc = float(pk.get("bf16_tflops", 1900.0)) * (1.0 if prec == "bf16x3" else 1.1 / 2.25)
+    out = {"bound": "hbm", "kernel": "k_contract_tc", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+           "frac": achieved / hbm, "bytes_per_step": op_bytes,
+           "peak_note": f"HBM copy bandwidth ({pk_kind})",
+           "tensor_tflops": flops / t / 1e12, "tensor_peak": peak_tc,
+           "tensor_frac": flops / t / 1e12 / peak_tc,
+           "tensor_peak_note": f"dense BF16 ({pk_kind}, burst)" + (" x 1.1/2.25 for TF32" if prec == "tf32" else "")}
+    if stages_ms.get("pack", 0.0) > 0.0:
+        pack_bytes = elems * 4.0 + op_bytes
+        out["pack"] = {"kernel": "k_pack", "achieved": pack_bytes / (stages_ms["pack"] / 1e3) / 1e9,
+                       "bytes_per_step": pack_bytes,
+                       "frac": pack_bytes / (stages_ms["pack"] / 1e3) / 1e9 / hbm}
+    return {"roofline_contraction": out}
 
 
 def peaks():
@@ -450,6 +474,7 @@ def run_ours(args):
     nc = ncoef(kw)
     sphere = bool(kw.get("sphere"))
     batch = isinstance(xyz, list)  # several catalogues, one ctb_compute_batch per step
+    negw = bool(any(np.any(v < 0) for v in w)) if batch else bool(np.any(w < 0))
     # precisions timed in this run: "mixed" = plain FP32, then the BF16 hi/lo
     # tensor-core contraction (the line's headline), then a short TF32 extra
     if args.precision == "mixed":
@@ -626,7 +651,8 @@ def run_ours(args):
             "pairs_per_step": r["npairs_all"], "pairs_per_s": args.steps_of(prec) * r["npairs_all"] / r["t_total"],
             "stages_ms": stages_ms, "gpu_launches": r["launches"],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                         "frac": achieved / peak_tinst, "traffic": None, **roof, "launches_per_step": r["chunks"],
+                         "frac": achieved / peak_tinst, "traffic": None, **roof,
+                         "launches_per_step": r["chunks"] * (1 if sphere else len(pass_split(kw["lmax"]))),
                          "peak_note": f"FP32 pipe: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
                                       f"{sm_max:.0f} MHz ({pk_kind} max clock), burst",
                          "kernel_ms": 1e3 * pair_s},
@@ -635,7 +661,7 @@ def run_ours(args):
             else args.primaries
         if world > 1 and d_prim is not None and not args.primaries:
             n_prim_step = int(d_prim.shape[0])
-        out.update(contraction_roofline(prec, kw, stages_ms, pk, pk_kind, npts=n_prim_step))
+        out.update(contraction_roofline(prec, kw, stages_ms, pk, pk_kind, npts=n_prim_step, negw=negw))
         return out
 
     args.steps_of = lambda prec: args.steps
