@@ -11,111 +11,199 @@ namespace ctb {
 
 // Register-tiled form.  For one l, zeta~_l restricted to bins [4B1, 4B1+4) x
 // [4B2, 4B2+4) is a 4x4 tile: per primary and per m, one 16-byte shared load
-// of each side (bins contiguous) and 16 FMAs.  Work split of a block:
-//   warp  -> a multipole pair (l, L - l) (one l when l = L - l), so every warp
-//            does 2L + 2 m-steps per primary and no lane diverges on l;
-//            pairs with more than 32 tiles take several warps
-//   lane  -> a tile B1 <= B2 and an m-group g: lanes of the same tile split the
-//            m-steps (m = g, g + G, ...) and are added in group order at the end
-// The block stages a few primaries' rows transposed to [primary][l^2+l+m][bin]
-// (bins padded to a multiple of 4 with zeros).  FP32 over the block's slice of
-// the launch's primaries, then one FP64 add per (l, b1 <= b2) entry, whose
-// owner is a single lane: the partial sums are deterministic.
+// of each side (four bins contiguous) and eight paired FMAs.  Work split of a
+// block: every (multipole pair (l, L - l), tile B1 <= B2) is a task, and G
+// consecutive threads share a task, splitting its m-steps (m = g, g + G,
+// ...) and adding their partial tiles in thread order at the end.  A pair
+// does 2L + 2 m-steps per primary whatever its l (one l when l = L - l), so
+// the threads of a warp stay in step.  All pairs of a primary fit one block
+// (up to 512 threads), so each row is read from HBM once; larger shapes
+// split the pairs over blockIdx.y.
+//
+// Staging: the block walks its slice of the launch's primaries in stages of
+// Q primaries, double-buffered in shared memory.  While the FMAs run on one
+// buffer, the next stage's rows are in flight in registers: a warp loads 4
+// bins x 8 float4 (one 128-byte line per bin), and each thread scatters its
+// float4 to the staged layout [slot][bin], slot s at row s * nbp + 4 (s / 8):
+// the 4 (s / 8) shift puts the 32 scalar stores of a warp (8 consecutive
+// slots x 4 bins) in 32 distinct banks when nbp = 4 mod 32.  Bins are padded
+// to a multiple of 4 with zeros.  When two buffers do not fit (64 bins at
+// l_max 20), one buffer is staged between two barriers, the next stage's
+// loads still in flight during the FMAs.  FP32 over the block's slice, then one FP64
+// add per (l, b1 <= b2) entry, whose owner is a single thread: the partial
+// sums are deterministic.
 constexpr int kConTile = 4;
 constexpr int kConMaxThreads = 512;
-constexpr int kConStageFloats = 10240;  // 40 KB of staged rows: several blocks per SM
+constexpr int kConStageFloats = 20480;  // one staged buffer at most (80 KB; two are used)
+constexpr int kConPF = 8;              // float4 loads a thread keeps in flight per stage
+constexpr size_t kConSmemCap = 220 * 1024;
+constexpr int kConMaxQ = 64;            // primaries per stage at most
 
 struct ConShape {
-  int nbb, tiles, G, warps_per_pair, pairs, pairs_per_block, ny, threads, Q, per, red_floats, tab_ints,
-      smem_floats;
+  int nbb;           // bin quads
+  int nbp;           // floats per staged slot row
+  int tiles;         // 4x4 tiles B1 <= B2
+  int pairs;         // multipole pairs (l, L - l)
+  int G;             // threads per task
+  int ppb, ny;       // pairs per block, blocks in y
+  int threads;
+  int nch;           // load chunks of 8 float4 along a row
+  int srow;          // floats per staged primary
+  int Q;             // primaries per stage
+  int nbuf;          // staged buffers: 2, or 1 when two do not fit
+  int tab_ints;      // coefficient -> slot table
+  int stage_floats;  // all buffers
+  int red_floats;    // the end-of-kernel combine buffer (aliases the stages)
+  int smem_floats;
 };
 
 __host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row, int sphere) {
   ConShape c{};
   c.nbb = (nbins + kConTile - 1) / kConTile;
+  c.nbp = kConTile * c.nbb;
+  if (c.nbp % 32 == 0) c.nbp += 4;
   c.tiles = c.nbb * (c.nbb + 1) / 2;
-  c.warps_per_pair = (c.tiles + 31) / 32;
-  c.G = c.tiles >= 32 ? 1 : 32 / c.tiles;
   c.pairs = lmax / 2 + 1;
-  // at most kConMaxThreads a block: more pairs go to further blocks in y
-  c.pairs_per_block = kConMaxThreads / (32 * c.warps_per_pair);
-  if (c.pairs_per_block > c.pairs) c.pairs_per_block = c.pairs;
-  c.ny = (c.pairs + c.pairs_per_block - 1) / c.pairs_per_block;
-  c.threads = 32 * c.warps_per_pair * c.pairs_per_block;
   const int nc = sphere ? 2 * lmax + 1 : (lmax + 1) * (lmax + 1);
-  c.per = nc * c.nbb * kConTile;
-  c.Q = c.per >= kConStageFloats ? 1 : kConStageFloats / c.per;
-  c.red_floats = c.G > 1 ? (c.threads / 32) * 32 * 17 : 0;
-  c.tab_ints = (row + 3) & ~3;  // row slot -> l^2 + l + m, or -1
-  c.smem_floats = c.tab_ints + c.Q * c.per + c.red_floats;
-  return c;
-}
-
-// 4x4 tile of one group (a multipole l: components l^2 .. l^2 + 2l; on the
-// sphere, m: component 0, or 2m-1 and 2m): acc[i][j] += w * sum_{c in group} x_i y_j,
-// the lanes of the tile's m-groups taking every G-th component.
-__device__ __forceinline__ void con_tile(const float* __restrict__ S, int nbp, int s0, int nc, int g, int G, int B1,
-                                         int B2, float w, float (&acc)[16]) {
-  for (int m = g; m < nc; m += G) {
-    const float4 x = *reinterpret_cast<const float4*>(S + (s0 + m) * nbp + 4 * B1);
-    const float4 y = *reinterpret_cast<const float4*>(S + (s0 + m) * nbp + 4 * B2);
-    const float xs[4] = {w * x.x, w * x.y, w * x.z, w * x.w};
-    const float ys[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i * 4 + j] = fmaf(xs[i], ys[j], acc[i * 4 + j]);
+  const int msteps = sphere ? 4 : 2 * lmax + 2;  // m-steps of the longest pair
+  if (c.pairs * c.tiles <= kConMaxThreads) {
+    c.ppb = c.pairs;
+    c.G = kConMaxThreads / (c.pairs * c.tiles);
+    if (c.G > msteps) c.G = msteps;
+    if (c.G > 32) c.G = 32;
+  } else {
+    c.G = 1;
+    c.ppb = kConMaxThreads / c.tiles;
   }
+  c.ny = (c.pairs + c.ppb - 1) / c.ppb;
+  c.threads = (c.ppb * c.tiles * c.G + 31) / 32 * 32;
+  c.nch = ((row + 3) / 4 + 7) / 8;
+  {
+    // enough warps that one primary's rows are in flight in registers
+    const int wl = (c.nbb * c.nch + kConPF - 1) / kConPF;
+    if (c.threads < 32 * wl) c.threads = 32 * wl < kConMaxThreads ? 32 * wl : kConMaxThreads;
+  }
+  c.srow = (row * c.nbp + 4 * ((row + 7) / 8) + 3) & ~3;
+  const int units1 = c.nbb * c.nch;  // load units of one primary
+  const int warps = c.threads / 32;
+  c.Q = kConStageFloats / c.srow;
+  if (c.Q * units1 > kConPF * warps) c.Q = kConPF * warps / units1;  // keep a stage's loads in registers
+  if (c.Q < 1) c.Q = 1;
+  if (c.Q > kConMaxQ) c.Q = kConMaxQ;
+  // coefficient -> staged row offset, then the staged primaries' weights
+  c.tab_ints = ((nc + 3) & ~3) + 2 * kConMaxQ;
+  c.nbuf = (size_t)(c.tab_ints + 2 * c.Q * c.srow) * 4 <= kConSmemCap ? 2 : 1;
+  c.stage_floats = c.nbuf * c.Q * c.srow;
+  c.red_floats = c.threads * 17;
+  c.smem_floats = c.tab_ints + (c.stage_floats > c.red_floats ? c.stage_floats : c.red_floats);
+  (void)nc;
+  return c;
 }
 
 __device__ __forceinline__ int group_start(int l, int sphere) { return sphere ? (l == 0 ? 0 : 2 * l - 1) : l * l; }
 __device__ __forceinline__ int group_size(int l, int sphere) { return sphere ? (l == 0 ? 1 : 2) : 2 * l + 1; }
 
-__device__ __forceinline__ void con_flush(const ConShape& sh, const float (&acc)[16], int l, int tile, int g, int B1,
-                                          int B2, int nb, int lmax, double* __restrict__ out, float* s_red,
-                                          int lane) {
-  // lanes of one tile: add the m-groups in order through shared memory
-  float* mine = s_red + lane * 17;
-  if (sh.G > 1) {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) mine[k] = acc[k];
+// offset of slot s of staged primary q
+__device__ __forceinline__ int con_off(const ConShape& sh, int q, int s) { return q * sh.srow + s * sh.nbp + 4 * (s >> 3); }
+
+// 4x4 tile of one group (a multipole l: components l^2 .. l^2 + 2l; on the
+// sphere, m: component 0, or 2m-1 and 2m): acc += w x y^T summed over the
+// group's components, the task's threads taking every G-th component.
+// acc[2 i + j] holds entries (i, 2j) and (i, 2j + 1).
+__device__ __forceinline__ void con_tile(const float* __restrict__ S, int G, const int* s_offc, int c0, int nc, int g,
+                                         int B1, int B2, float w, float2 (&acc)[8]) {
+  const float* Sx = S + 4 * B1;
+  const float* Sy = S + 4 * B2;
+#pragma unroll 2
+  for (int m = g; m < nc; m += G) {
+    const int off = s_offc[c0 + m];
+    const float4 x = *reinterpret_cast<const float4*>(Sx + off);
+    const float4 y = *reinterpret_cast<const float4*>(Sy + off);
+    const float2 y01 = make_float2(y.x, y.y), y23 = make_float2(y.z, y.w);
+    const float2 x01 = __fmul2_rn(make_float2(w, w), make_float2(x.x, x.y));
+    const float2 x23 = __fmul2_rn(make_float2(w, w), make_float2(x.z, x.w));
+    acc[0] = __ffma2_rn(make_float2(x01.x, x01.x), y01, acc[0]);
+    acc[1] = __ffma2_rn(make_float2(x01.x, x01.x), y23, acc[1]);
+    acc[2] = __ffma2_rn(make_float2(x01.y, x01.y), y01, acc[2]);
+    acc[3] = __ffma2_rn(make_float2(x01.y, x01.y), y23, acc[3]);
+    acc[4] = __ffma2_rn(make_float2(x23.x, x23.x), y01, acc[4]);
+    acc[5] = __ffma2_rn(make_float2(x23.x, x23.x), y23, acc[5]);
+    acc[6] = __ffma2_rn(make_float2(x23.y, x23.y), y01, acc[6]);
+    acc[7] = __ffma2_rn(make_float2(x23.y, x23.y), y23, acc[7]);
   }
-  __syncwarp();
-  if (g == 0 && tile < sh.tiles && l <= lmax) {
+}
+
+// The G threads of a task add their tiles in thread order (through shared
+// memory), and the first adds the result to the block's FP64 partial.
+__device__ __forceinline__ void con_flush(const ConShape& sh, const float2 (&acc)[8], bool own, int l, int g,
+                                          int B1, int B2, int nb, double* __restrict__ out, float* s_red) {
+  float* mine = s_red + threadIdx.x * 17;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    mine[2 * k] = acc[k].x;
+    mine[2 * k + 1] = acc[k].y;
+  }
+  __syncthreads();
+  if (own && g == 0) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      float v = acc[k];
-      for (int h = 1; h < sh.G; ++h) v += s_red[(lane + h * sh.tiles) * 17 + k];
-      const int b1 = 4 * B1 + k / 4, b2 = 4 * B2 + k % 4;
+      float v = mine[k];
+      for (int h = 1; h < sh.G; ++h) v += s_red[(threadIdx.x + h) * 17 + k];
+      // k = 2 (2 i + j') + e: entry (i, 2 j' + e)
+      const int i = k >> 2, j = k & 3;
+      const int b1 = 4 * B1 + i, b2 = 4 * B2 + j;
       if (b1 < nb && b2 < nb && b1 <= b2) out[((size_t)l * nb + b1) * nb + b2] += (double)v;
     }
   }
-  __syncwarp();
+  __syncthreads();
+}
+
+// Load units: 4 bins x 8 float4 of a row (lane l: bin 4 bq + l / 8, float4
+// 8 ch + l % 8) of staged primary q, u = (q nbb + bq) nch + ch.  Warp w owns
+// units [w upw, (w + 1) upw) of a stage, walked by incrementing (q, bq, ch).
+struct ConUnit {
+  int q, bq, ch;
+};
+__device__ __forceinline__ void con_next(const ConShape& sh, ConUnit& t) {
+  if (++t.ch == sh.nch) {
+    t.ch = 0;
+    if (++t.bq == sh.nbb) {
+      t.bq = 0;
+      ++t.q;
+    }
+  }
+}
+
+__device__ __forceinline__ void con_store4(float* buf, const ConShape& sh, int q, int b, int c4, float4 v) {
+  const int s = 4 * c4;
+  float* d = buf + con_off(sh, q, s) + b;
+  // slots s .. s + 3 share s / 8
+  d[0] = v.x;
+  d[sh.nbp] = v.y;
+  d[2 * sh.nbp] = v.z;
+  d[3 * sh.nbp] = v.w;
 }
 
 __global__ void __launch_bounds__(kConMaxThreads, 1) k_contract_fp32(ContractArgs a) {
-  extern __shared__ float s_dyn[];
+  extern __shared__ __align__(16) float s_dyn[];
   const int nb = a.nbins, L = a.lmax;
   const int nc = a.sphere ? 2 * L + 1 : (L + 1) * (L + 1);  // coefficients per (primary, bin)
   const ConShape sh = con_shape(nb, L, a.row, a.sphere);
-  const int nbp = sh.nbb * kConTile;
-  const int per = sh.per;
-  // [row slot -> coefficient table | Q staged primaries | per-warp m-group combine buffers]
-  int* s_inv = reinterpret_cast<int*>(s_dyn);
-  float* s_rows = s_dyn + sh.tab_ints;
-  float* s_red_all = s_rows + sh.Q * per;
-  for (int k = threadIdx.x; k < a.row; k += blockDim.x) s_inv[k] = -1;
-  for (int k = threadIdx.x; k < sh.Q * per; k += blockDim.x) s_rows[k] = 0.f;  // bin padding stays zero
-  __syncthreads();
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) s_inv[a.slot[c]] = c;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int pair = blockIdx.y * sh.pairs_per_block + warp / sh.warps_per_pair;
-  const int part = warp % sh.warps_per_pair;
-  const int la = pair, lb = L - pair;
-  const int tl = lane % (sh.G == 1 ? 32 : sh.tiles);
-  const int g = sh.G == 1 ? 0 : lane / sh.tiles;
-  const int tile = part * 32 + tl;
-  const bool active = pair < sh.pairs && tile < sh.tiles && g < sh.G;
+  // [coefficient -> staged row offset | weights of the staged primaries, per
+  //  buffer | staged buffers (the combine buffer at the end)]
+  int* s_offc = reinterpret_cast<int*>(s_dyn);
+  float* s_w = s_dyn + (sh.tab_ints - 2 * kConMaxQ);
+  float* s_stage = s_dyn + sh.tab_ints;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const int sl = a.slot[c];
+    s_offc[c] = sl * sh.nbp + 4 * (sl >> 3);
+  }
+  for (int k = threadIdx.x; k < sh.stage_floats; k += blockDim.x) s_stage[k] = 0.f;  // bin padding stays zero
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int task = tid / sh.G, g = tid - task * sh.G;
+  const int pair = blockIdx.y * sh.ppb + task / sh.tiles;
+  const int tile = task % sh.tiles;
+  const bool active = task < sh.ppb * sh.tiles && pair < sh.pairs;
   int B1 = 0, B2 = 0;
   {
     int r = active ? tile : 0;
@@ -125,68 +213,119 @@ __global__ void __launch_bounds__(kConMaxThreads, 1) k_contract_fp32(ContractArg
     }
     B2 = B1 + r;
   }
-  float acc_a[16], acc_b[16];
+  const int la = pair, lb = L - pair;
+  float2 acc_a[8], acc_b[8];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) acc_a[k] = acc_b[k] = 0.f;
+  for (int k = 0; k < 8; ++k) acc_a[k] = acc_b[k] = make_float2(0.f, 0.f);
   const int64_t slice = (a.np + gridDim.x - 1) / gridDim.x;
   const int64_t p0 = (int64_t)blockIdx.x * slice;
   const int64_t p1 = min(a.np, p0 + slice);
-  const int rowsz = nb * a.row;
+  const int64_t rowsz = (int64_t)nb * a.row;
   const bool vec4 = (a.row & 3) == 0 && (reinterpret_cast<uintptr_t>(a.M) & 15) == 0;
-  for (int64_t pb = p0; pb < p1; pb += sh.Q) {
-    const int cnt = (int)min((int64_t)sh.Q, p1 - pb);
-    __syncthreads();  // the previous primaries are done (and the tables / zero fill on entry)
-    // coalesced loads of the rows (16 bytes when rows and base allow it),
-    // scattered to [primary][coefficient][bin]
-    if (vec4) {
-      // consecutive lanes take consecutive bins of the same four slots: their
-      // transposed stores land in consecutive words (no bank conflicts)
-      const float4* src = reinterpret_cast<const float4*>(a.M + (uint64_t)pb * rowsz);
-      const int row4 = a.row >> 2;
-      for (int k = threadIdx.x; k < cnt * nb * row4; k += blockDim.x) {
-        const int r = k / nb, b = k - r * nb;  // r = primary * row4 + c4
-        const int q = r / row4, c4 = r - q * row4;
-        const float4 v = __ldcs(src + ((q * nb + b) * row4 + c4));
-        const float e[4] = {v.x, v.y, v.z, v.w};
-        float* dst = s_rows + q * per + b;
+  const int row4 = a.row >> 2;
+  const int units = sh.Q * sh.nbb * sh.nch;  // load units of a full stage
+  const int upw = (units + nwarps - 1) / nwarps;   // units per warp
+  ConUnit t0;  // this warp's first unit
+  {
+    const int u0 = warp * upw, per = sh.nbb * sh.nch;
+    t0.q = u0 / per;
+    t0.bq = (u0 - t0.q * per) / sh.nch;
+    t0.ch = u0 - t0.q * per - t0.bq * sh.nch;
+  }
+  const int lb8 = lane >> 3, lc8 = lane & 7;
+  __syncthreads();
+
+  // rows of the stage at pb (cnt primaries) into buffer buf: the warp's
+  // first kConPF units from registers (loaded by issue), the rest here
+  float4 pf[kConPF];
+  float wpf = 0.f;  // thread q < Q: the weight of staged primary q
+  auto issue = [&](int64_t pb, int cnt) {
+    if (tid < cnt) wpf = __ldg(a.wprim + pb + tid);
+    const float4* src = reinterpret_cast<const float4*>(a.M + pb * rowsz);
+    ConUnit t = t0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = s_inv[4 * c4 + i];
-          if (c >= 0) dst[c * nbp] = e[i];
-        }
-      }
-    } else {
-      const float* src = a.M + (uint64_t)pb * rowsz;
-      for (int k = threadIdx.x; k < cnt * nb * a.row; k += blockDim.x) {
-        const int pr = k / a.row, sl = k - pr * a.row;
-        const int q = pr / nb, b = pr - q * nb;
-        const int c = s_inv[sl];
-        if (c >= 0) s_rows[q * per + c * nbp + b] = __ldcs(src + k);
-      }
+    for (int i = 0; i < kConPF; ++i) {
+      const int b = 4 * t.bq + lb8, c4 = 8 * t.ch + lc8;
+      if (i < upw && t.q < cnt && b < nb && c4 < row4) pf[i] = __ldcs(src + ((int64_t)t.q * nb + b) * row4 + c4);
+      con_next(sh, t);
     }
-    __syncthreads();
-    if (active) {
-      for (int q = 0; q < cnt; ++q) {
-        const float w = a.wprim[pb + q];
-        const float* S = s_rows + q * per;
-        con_tile(S, nbp, group_start(la, a.sphere), group_size(la, a.sphere), g, sh.G, B1, B2, w, acc_a);
-        if (lb != la)
-          con_tile(S, nbp, group_start(lb, a.sphere), group_size(lb, a.sphere), g, sh.G, B1, B2, w, acc_b);
-      }
+  };
+  auto land = [&](float* buf, int64_t pb, int cnt) {
+    if (tid < cnt) s_w[(buf == s_stage ? 0 : kConMaxQ) + tid] = wpf;
+    ConUnit t = t0;
+#pragma unroll
+    for (int i = 0; i < kConPF; ++i) {
+      const int b = 4 * t.bq + lb8, c4 = 8 * t.ch + lc8;
+      if (i < upw && t.q < cnt && b < nb && c4 < row4) con_store4(buf, sh, t.q, b, c4, pf[i]);
+      con_next(sh, t);
+    }
+    const float4* src = reinterpret_cast<const float4*>(a.M + pb * rowsz);
+    for (int i = kConPF; i < upw; ++i) {
+      const int b = 4 * t.bq + lb8, c4 = 8 * t.ch + lc8;
+      if (t.q < cnt && b < nb && c4 < row4)
+        con_store4(buf, sh, t.q, b, c4, __ldcs(src + ((int64_t)t.q * nb + b) * row4 + c4));
+      con_next(sh, t);
+    }
+  };
+  // scalar rows (a row length that is not a multiple of 4, or an unaligned base)
+  auto land1 = [&](float* buf, int64_t pb, int cnt) {
+    if (tid < cnt) s_w[(buf == s_stage ? 0 : kConMaxQ) + tid] = __ldg(a.wprim + pb + tid);
+    const float* src = a.M + pb * rowsz;
+    for (int64_t k = tid; k < (int64_t)cnt * rowsz; k += blockDim.x) {
+      const int64_t pr = k / a.row;
+      const int s = (int)(k - pr * a.row);
+      const int q = (int)(pr / nb), b = (int)(pr - (int64_t)q * nb);
+      buf[con_off(sh, q, s) + b] = __ldcs(src + k);
+    }
+  };
+
+  int cur = 0;
+  if (p0 < p1) {
+    const int cnt = (int)min((int64_t)sh.Q, p1 - p0);
+    if (vec4) {
+      issue(p0, cnt);
+      land(s_stage, p0, cnt);
+    } else {
+      land1(s_stage, p0, cnt);
     }
   }
-  if (pair >= sh.pairs) return;
+  __syncthreads();
+  for (int64_t pb = p0; pb < p1; pb += sh.Q) {
+    const int cnt = (int)min((int64_t)sh.Q, p1 - pb);
+    const int64_t pn = pb + sh.Q;
+    const int cntn = pn < p1 ? (int)min((int64_t)sh.Q, p1 - pn) : 0;
+    float* bufc = s_stage + cur * sh.Q * sh.srow;
+    float* bufn = s_stage + (sh.nbuf == 2 ? cur ^ 1 : 0) * sh.Q * sh.srow;
+    if (vec4 && cntn > 0) issue(pn, cntn);  // in flight during the FMAs
+    if (active) {
+      const float* wq = s_w + (bufc == s_stage ? 0 : kConMaxQ);
+      for (int q = 0; q < cnt; ++q) {
+        const float w = wq[q];
+        const float* S = bufc + q * sh.srow;
+        con_tile(S, sh.G, s_offc, group_start(la, a.sphere), group_size(la, a.sphere), g, B1, B2, w, acc_a);
+        if (lb != la) con_tile(S, sh.G, s_offc, group_start(lb, a.sphere), group_size(lb, a.sphere), g, B1, B2, w, acc_b);
+      }
+    }
+    if (cntn > 0) {
+      if (sh.nbuf == 1) __syncthreads();  // one buffer: every thread is done reading it
+      if (vec4) land(bufn, pn, cntn);
+      else land1(bufn, pn, cntn);
+    }
+    __syncthreads();  // bufc is read no more; bufn is staged
+    if (sh.nbuf == 2) cur ^= 1;
+  }
+  if (blockIdx.y * sh.ppb >= sh.pairs) return;  // the whole block has no pair (uniform)
   double* out = a.partial + (size_t)(a.part0 + blockIdx.x) * (L + 1) * nb * nb;
-  float* s_red = s_red_all + warp * 32 * 17;
-  con_flush(sh, acc_a, la, tile, g, B1, B2, nb, L, out, s_red, lane);
-  if (lb != la) con_flush(sh, acc_b, lb, tile, g, B1, B2, nb, L, out, s_red, lane);
+  float* s_red = s_stage;  // the stages are done
+  con_flush(sh, acc_a, active && la <= L, la, g, B1, B2, nb, out, s_red);
+  con_flush(sh, acc_b, active && lb != la && lb >= 0, lb, g, B1, B2, nb, out, s_red);
 }
 
 // Resident blocks per SM of the contraction for this shape (0 if it cannot run).
 int contract_fp32_blocks_per_sm(int nbins, int lmax, int row, int sphere) {
   const ConShape sh = con_shape(nbins, lmax, row, sphere);
   const size_t smem = (size_t)sh.smem_floats * sizeof(float);
-  if (smem > 200 * 1024) return 0;
+  if (smem > kConSmemCap) return 0;
   if (cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int nb = 0;
@@ -198,7 +337,7 @@ cudaError_t launch_contract_fp32(const ContractArgs& a, int nparts, cudaStream_t
   if (a.np == 0) return cudaSuccess;
   const ConShape sh = con_shape(a.nbins, a.lmax, a.row, a.sphere);
   const size_t smem = (size_t)sh.smem_floats * sizeof(float);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > kConSmemCap) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_contract_fp32<<<dim3(nparts, sh.ny), sh.threads, smem, st>>>(a);
