@@ -56,7 +56,7 @@ INST_PER_UPDATE = 2.6
 # the captured launches, summed over the m-pass launches of one chunk: one at
 # l_max 10, three at l_max 20).  Keyed by l_max; a missing entry reports null
 # traffic.
-K_ALM_DRAM_BYTES_PER_PAIR = {10: 4.385, 20: 21.17}
+K_ALM_DRAM_BYTES_PER_PAIR = {10: 4.383, 20: 21.17}
 FP32_LANES_PER_SM = 128
 
 
