@@ -27,7 +27,10 @@ namespace ctb {
 // float4 to the staged layout [slot][bin], slot s at row s * nbp + 4 (s / 8):
 // the 4 (s / 8) shift puts the 32 scalar stores of a warp (8 consecutive
 // slots x 4 bins) in 32 distinct banks when nbp = 4 mod 32.  Bins are padded
-// to a multiple of 4 with zeros.  When two buffers do not fit (64 bins at
+// to a multiple of 4 with zeros.  Shapes whose tasks fit 256 threads (short
+// rows: the sphere's, l_max 10) run two such blocks per SM with half-size
+// stages; the stage size of short rows is raised with extra loader warps so
+// that a stage still fits the registers.  When two buffers do not fit (64 bins at
 // l_max 20), one buffer is staged between two barriers, the next stage's
 // loads still in flight during the FMAs.  FP32 over the block's slice, then one FP64
 // add per (l, b1 <= b2) entry, whose owner is a single thread: the partial
@@ -38,6 +41,9 @@ constexpr int kConStageFloats = 20480;  // one staged buffer at most (80 KB; two
 constexpr int kConPF = 8;              // float4 loads a thread keeps in flight per stage
 constexpr size_t kConSmemCap = 220 * 1024;
 constexpr int kConMaxQ = 64;            // primaries per stage at most
+// shapes whose tasks fit this many threads run two blocks per SM (half the
+// threads, half the staged rows each: 2 x 256 threads x 128 registers)
+constexpr int kConSmallThreads = 256;
 
 struct ConShape {
   int nbb;           // bin quads
@@ -66,9 +72,11 @@ __host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row, int 
   c.pairs = lmax / 2 + 1;
   const int nc = sphere ? 2 * lmax + 1 : (lmax + 1) * (lmax + 1);
   const int msteps = sphere ? 4 : 2 * lmax + 2;  // m-steps of the longest pair
+  const bool small = c.pairs * c.tiles <= kConSmallThreads;
+  const int tmax = small ? kConSmallThreads : kConMaxThreads;
   if (c.pairs * c.tiles <= kConMaxThreads) {
     c.ppb = c.pairs;
-    c.G = kConMaxThreads / (c.pairs * c.tiles);
+    c.G = tmax / (c.pairs * c.tiles);
     if (c.G > msteps) c.G = msteps;
     if (c.G > 32) c.G = 32;
   } else {
@@ -81,15 +89,23 @@ __host__ __device__ inline ConShape con_shape(int nbins, int lmax, int row, int 
   {
     // enough warps that one primary's rows are in flight in registers
     const int wl = (c.nbb * c.nch + kConPF - 1) / kConPF;
-    if (c.threads < 32 * wl) c.threads = 32 * wl < kConMaxThreads ? 32 * wl : kConMaxThreads;
+    if (c.threads < 32 * wl) c.threads = 32 * wl < tmax ? 32 * wl : tmax;
   }
   c.srow = (row * c.nbp + 4 * ((row + 7) / 8) + 3) & ~3;
   const int units1 = c.nbb * c.nch;  // load units of one primary
+  int q = (small ? kConStageFloats / 2 : kConStageFloats) / c.srow;
+  if (q > kConMaxQ) q = kConMaxQ;
+  if (q < 1) q = 1;
+  {
+    // short rows: more warps (idle in the FMAs) so that a stage of q
+    // primaries is still loaded from registers
+    const int wq = (q * units1 + kConPF - 1) / kConPF;
+    if (c.threads < 32 * wq) c.threads = 32 * wq < tmax ? 32 * wq : tmax;
+  }
   const int warps = c.threads / 32;
-  c.Q = kConStageFloats / c.srow;
+  c.Q = q;
   if (c.Q * units1 > kConPF * warps) c.Q = kConPF * warps / units1;  // keep a stage's loads in registers
   if (c.Q < 1) c.Q = 1;
-  if (c.Q > kConMaxQ) c.Q = kConMaxQ;
   // coefficient -> staged row offset, then the staged primaries' weights
   c.tab_ints = ((nc + 3) & ~3) + 2 * kConMaxQ;
   c.nbuf = (size_t)(c.tab_ints + 2 * c.Q * c.srow) * 4 <= kConSmemCap ? 2 : 1;
