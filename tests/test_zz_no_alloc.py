@@ -145,3 +145,23 @@ def test_noalloc_zero_primaries_and_argument_checks():
     for a, ww, o in bad:
         with pytest.raises(ValueError):
             ctb.contract_noalloc(a, ww, nbins, lmax, o)
+
+
+@pytest.mark.parametrize("nbins,lmax,npr", [(1, 0, 50), (3, 2, 200), (4, 3, 300), (7, 5, 130), (20, 8, 400),
+                                            (40, 9, 100), (64, 3, 64), (12, 1, 1000)])
+def test_noalloc_shapes_against_oracle(nbins, lmax, npr):
+    """The contraction's shape-dependent paths (threads per task, stage size,
+    two blocks per SM, the scalar staging of rows whose length is not a
+    multiple of 4) on random rows with weights of both signs."""
+    torch, ctb = _lib()
+    dev = torch.device("cuda")
+    g = torch.Generator(device="cpu").manual_seed(1000 * nbins + lmax)
+    alm = torch.randn((npr, nbins, (lmax + 1) ** 2), generator=g, dtype=torch.float32).to(dev)
+    wp = (torch.rand((npr,), generator=g, dtype=torch.float32) * 2.0 - 0.5).to(dev)
+    ref = _contract_ref(alm, wp, lmax)
+    out = torch.full((lmax + 1, nbins, nbins), float("nan"), dtype=torch.float64, device=dev)
+    ctb.contract_noalloc(alm, wp, nbins, lmax, out)
+    torch.cuda.synchronize()
+    z = out.cpu().numpy()
+    assert np.all(np.isfinite(z))
+    assert zeta_err(z, ref) < TOL_FP32
