@@ -68,7 +68,7 @@ typedef struct ctb_ctx ctb_ctx;
 #define CTB_OPT_PRECISION 1      /* contraction precision, CTB_PREC_* (default FP32)        */
 #define CTB_OPT_CELLS_PER_RMAX 2 /* grid cells per r_max along an axis, 1..64 (0 = auto)    */
 #define CTB_OPT_LIST_CAPACITY 3  /* neighbour-list entries per chunk, 4096..2^32 (0 = 2^32) */
-#define CTB_OPT_WARPS_PER_BLOCK 4/* pair-kernel warps per block, 1..16 (0 = auto)           */
+#define CTB_OPT_WARPS_PER_BLOCK 4/* pair-kernel warps per block, 1..4 (0 = auto: 4)         */
 #define CTB_OPT_CHUNK_PRIMARIES 5/* primaries per pair-kernel launch, >= 1024 (0 = auto)    */
 #define CTB_OPT_DETERMINISTIC 6  /* 1: fixed reduction order (default 1)                    */
 #define CTB_OPT_AUTOTUNE 7       /* 1: time the grid cell sizes on the next set_points    */

@@ -1447,7 +1447,8 @@ int ctb_set_option(ctb_ctx* c, int key, int64_t v) {
       c->list_cap = v == 0 ? (uint64_t)1 << 32 : (uint64_t)v;
       return CTB_OK;
     case CTB_OPT_WARPS_PER_BLOCK:
-      if (v < 0 || v > 16) return fail(c, CTB_ERR_ARG, "warps per block out of range [0, 16]");
+      // the pair kernels are compiled for blocks of at most 128 threads
+      if (v < 0 || v > 4) return fail(c, CTB_ERR_ARG, "warps per block out of range [0, 4]");
       c->wpb = (int)v;
       return CTB_OK;
     case CTB_OPT_CHUNK_PRIMARIES:

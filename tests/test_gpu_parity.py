@@ -263,6 +263,12 @@ def test_errors_are_status_codes(ctbmod):
     with pytest.raises(ctbmod.CTBError) as e:
         est.compute_subset(np.array([0, 7]))
     assert e.value.code == ctbmod.ERR_ARG
+    # the pair kernels take blocks of at most 4 warps
+    with pytest.raises(ctbmod.CTBError) as e:
+        est.set_option(ctbmod.OPT_WARPS_PER_BLOCK, 5)
+    assert e.value.code == ctbmod.ERR_ARG
+    est.set_option(ctbmod.OPT_WARPS_PER_BLOCK, 2)
+    est.compute()
 
 
 def test_device_pointers_in_and_out(ctbmod):
