@@ -44,7 +44,7 @@ def alm_err(a, a_ref, w1_sum, lmax):
 
 def zeta_err_elementwise(z, ref, floor=1e-3):
     """Plain relative error max |dzeta| / |zeta_ref| over the entries with
-    |zeta_ref| >= floor * max_l |zeta_ref| (the survey's secondary metric)."""
+    |zeta_ref| >= floor * max_l |zeta_ref| (a secondary metric beside the Gram one)."""
     zr = ref["zeta"]
     big = np.abs(zr) >= floor * np.abs(zr).max(axis=(1, 2), keepdims=True)
     big &= np.abs(zr) > 0
@@ -54,7 +54,7 @@ def zeta_err_elementwise(z, ref, floor=1e-3):
 
 def zeta_err_normwise(z, ref):
     """Per-l normwise error max_(b1,b2) |dzeta_l| / max_(b1,b2) |zeta_ref_l|,
-    the largest over l (the survey's other secondary metric)."""
+    the largest over l (the other secondary metric)."""
     zr = ref["zeta"]
     d = np.abs(np.asarray(z) - zr).max(axis=(1, 2))
     m = np.abs(zr).max(axis=(1, 2))
