@@ -55,7 +55,7 @@ typedef struct ctb_ctx ctb_ctx;
 #define CTB_ERR_CUDA (-4)       /* a CUDA call or kernel launch failed            */
 #define CTB_ERR_TIMEOUT (-5)    /* a bounded device-side wait gave up             */
 #define CTB_ERR_STATE (-6)      /* call out of order (e.g. compute before points) */
-#define CTB_ERR_UNSUPPORTED (-7)/* option value not available in this build       */
+#define CTB_ERR_UNSUPPORTED (-7)/* option value or mode the library does not offer */
 
 /* largest ell_max a context accepts */
 #define CTB_LMAX_CAP 20
@@ -239,7 +239,7 @@ int ctb_compute_batch(ctb_ctx* ctx, const double* const* xyz, const double* cons
                       const int64_t* n, int k, double* zeta_out);
 
 /* Set an option (CTB_OPT_*).  Returns CTB_ERR_ARG for an unknown key or a value
- * out of range, CTB_ERR_UNSUPPORTED for a precision this build cannot run.
+ * out of range, CTB_ERR_UNSUPPORTED for a precision the library cannot run.
  * CTB_OPT_LIST_CAPACITY bounds the neighbour lists of one chunk of primaries
  * (4 bytes per entry) and the candidates' bin codes of that chunk (1 byte per
  * candidate, at most 4 per list entry of the capacity); chunks are sized to
